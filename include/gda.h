@@ -1,0 +1,184 @@
+/*
+ * gda.h — C ABI of the GB300 gain-dissipative (GD) solver.
+ *
+ * The library time-steps R independent restarts of the GD rate equations of
+ * Kalinin & Berloff, "Global optimization of spin Hamiltonians with
+ * gain-dissipative systems" (2018):
+ *
+ *   dpsi_i/dt   = psi_i (gamma_i - |psi_i|^2) + beta * sum_{j != i} J_ij psi_j + h_1i   (Eq. 2)
+ *   dgamma_i/dt = eps (rho_th - |psi_i|^2)                                           (Eq. 5)
+ *   dbeta/dt    = eps_hat (1 - beta)        (Eq. 6 with Delta_ij = 1, K(t) = beta(t) J)
+ *
+ * with h_1i = -g_i sqrt(rho_th) and optional Euler-Maruyama noise D xi_i, and
+ * evaluates the spin Hamiltonian of Eq. (1),
+ *
+ *   H = - sum_i sum_j J_ij cos(theta_i - theta_j) + sum_i g_i cos(theta_i),
+ *
+ * on the projected spins of every restart.  Ising runs use real amplitudes
+ * (theta in {0, pi}); XY runs use complex amplitudes.
+ *
+ * Conventions for every entry point:
+ *   - Host pointers are plain C arrays owned by the caller; the library copies
+ *     what it needs and never keeps a host pointer after the call returns.
+ *   - `_dev` entry points take device pointers (e.g. torch data pointers) on
+ *     the context's device; the caller keeps ownership.
+ *   - The context owns all device memory it allocates; gda_destroy frees it.
+ *   - Work is queued on the context's stream (gda_set_stream; default: the
+ *     legacy default stream).  gda_run returns after queuing; device-side
+ *     errors (divergence, a barrier timeout) are reported by the next
+ *     synchronising call (gda_sync, gda_energy, gda_best, gda_get_state,
+ *     gda_trace).
+ *   - Every call returns a gda_status; on failure the context keeps a
+ *     message readable with gda_last_error.  No C++ exception crosses the ABI.
+ *   - Calls on one context are not thread safe; use one context per thread.
+ */
+#ifndef GDA_H
+#define GDA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gda_ctx gda_ctx;
+
+typedef enum {
+  GDA_ISING = 0, /* real amplitudes, spins s_i = sign(psi_i)            */
+  GDA_XY = 1     /* complex amplitudes, spins s_i = psi_i / |psi_i|     */
+} gda_model;
+
+typedef enum {
+  GDA_OK = 0,
+  GDA_ERR_INVALID = 1,     /* bad argument (sizes, NaN/asymmetric J, NULL)  */
+  GDA_ERR_CUDA = 2,        /* a CUDA runtime/driver call failed              */
+  GDA_ERR_OOM = 3,         /* device allocation failed                       */
+  GDA_ERR_DIVERGED = 4,    /* a non-finite or overflowing amplitude appeared */
+  GDA_ERR_TIMEOUT = 5,     /* a device-side wait ran out of its time limit   */
+  GDA_ERR_UNSUPPORTED = 6, /* option not available on this device / build    */
+  GDA_ERR_STATE = 7        /* call out of order (e.g. gda_energy before run) */
+} gda_status;
+
+typedef enum { GDA_EULER = 0, GDA_RK4 = 1 } gda_integrator;
+
+typedef enum {
+  GDA_FP32 = 0, /* J.Psi on CUDA cores in FP32 (the plain reference path)     */
+  GDA_BF16 = 1  /* J.Psi on tcgen05 tensor cores, BF16 operands, FP32 accum   */
+} gda_precision;
+
+/* Run parameters (Eqs. 2, 5, 6; Sec. 2 integrator).  Fill with
+ * gda_default_params, then override.  All rates are per unit of time t. */
+typedef struct {
+  int32_t integ;        /* gda_integrator                                      */
+  int32_t prec;         /* gda_precision of the coupling product               */
+  double dt;            /* time step                                           */
+  double eps;           /* gain adjustment speed epsilon, Eq. (5)              */
+  double rho_th;        /* threshold density rho_th, Eq. (5)                   */
+  double gamma0;        /* initial effective gain gamma^inj - gamma_c          */
+  double beta0;         /* initial coupling scale, K(0) = beta0 J              */
+  double eps_hat;       /* coupling adjustment speed, Eq. (6)                  */
+  double noise_D;       /* noise strength D, Eq. (2); 0 disables noise         */
+  int32_t noise_decay;  /* 1: D_r = D max(0, 1 - mean_i rho_i / rho_th)        */
+  int32_t energy_every; /* k > 0: record the best projected energy every k steps */
+  uint64_t seed;        /* Philox4x32-10 key for noise and initial amplitudes  */
+  int32_t init_mode;    /* 0: psi = 0; 1: seeded U(-a, a) per real component;
+                           2: continue from the current state (resume)        */
+  int32_t reserved0;
+  double init_amp;      /* a for init_mode 1                                   */
+} gda_params;
+
+/* Fills p with dt = 0.01, eps = 0.1, rho_th = 1, gamma0 = 0, beta0 = 1,
+ * eps_hat = 0, noise off, Euler, FP32, init_mode 1 with a = 1e-3, seed 0. */
+void gda_default_params(gda_params* p);
+
+/* Creates a context for an N-spin instance on the current CUDA device.
+ * J: N*N row-major doubles (host), symmetric and finite, copied.  The
+ *    diagonal is left out of the dynamics (Eq. 2 sums j != i) but counted in
+ *    the energy (Eq. 1 sums all ordered pairs).
+ * g: N doubles (host) or NULL for g = 0.
+ * Errors: GDA_ERR_INVALID for N < 1, N > 65536, NULL J or out, non-finite or
+ * asymmetric J, non-finite g, or model not in gda_model; GDA_ERR_OOM/CUDA.
+ * On failure *out is NULL. */
+gda_status gda_create(const double* J, const double* g, int32_t N, int32_t model, gda_ctx** out);
+
+/* Replaces J and g of an existing context with a new instance of the same N
+ * (host pointers, copied).  Same checks as gda_create.  Ordered on the stream. */
+gda_status gda_load(gda_ctx* ctx, const double* J, const double* g);
+
+/* Same as gda_load with device pointers (N*N and N doubles on the device). */
+gda_status gda_load_dev(gda_ctx* ctx, const double* J_dev, const double* g_dev);
+
+/* Sets the CUDA stream (a cudaStream_t passed as void*) used by every later
+ * call.  NULL selects the legacy default stream. */
+gda_status gda_set_stream(gda_ctx* ctx, void* stream);
+
+/* Runs `steps` steps for R restarts with parameters p (Eqs. 2, 5, 6).
+ * init_mode 0/1 starts a new run at step 0; init_mode 2 continues from the
+ * current state (R must equal the current restart count).  If
+ * p->energy_every = k > 0, the best projected energy over the restarts
+ * (FP32 tracking value) is recorded after every k-th step (gda_trace).
+ * Asynchronous on the context's stream.
+ * Errors: GDA_ERR_INVALID (R < 1, steps < 0, dt <= 0, non-finite params),
+ * GDA_ERR_UNSUPPORTED (BF16 on a device other than sm_103), GDA_ERR_OOM. */
+gda_status gda_run(gda_ctx* ctx, const gda_params* p, int32_t R, int64_t steps);
+
+/* Waits for the stream and reports device-side errors of earlier runs
+ * (GDA_ERR_DIVERGED, GDA_ERR_TIMEOUT).  The error flags are cleared. */
+gda_status gda_sync(gda_ctx* ctx);
+
+/* Eq. (1) energy of the projected spins of every restart, in FP64 (exact,
+ * through an int64 reduction, for Ising runs with integer J and g = 0).
+ * E: R doubles on the host.  Synchronises. */
+gda_status gda_energy(gda_ctx* ctx, double* E);
+
+/* Same as gda_energy into R doubles on the device; stream ordered, does not
+ * synchronise. */
+gda_status gda_energy_dev(gda_ctx* ctx, double* E_dev);
+
+/* Lowest Eq. (1) energy over the restarts (ties: lowest restart index).
+ * E, r: host scalars (either may be NULL).  cfg (may be NULL): N int8 spins
+ * (+1/-1) for Ising, or N doubles theta_i in (-pi, pi] for XY, host.
+ * Synchronises. */
+gda_status gda_best(gda_ctx* ctx, double* E, int32_t* r, void* cfg);
+
+/* Copies the state out (host).  psi: R*N floats (Ising) or R*N interleaved
+ * (re, im) float pairs (XY), restart-major; gamma: R*N floats; beta: R
+ * floats; step: global step count.  Any pointer may be NULL.  Synchronises. */
+gda_status gda_get_state(gda_ctx* ctx, float* psi, float* gamma, float* beta, int64_t* step);
+
+/* Sets the state (host arrays in the layout of gda_get_state) for R restarts
+ * at global step `step`; a following gda_run with init_mode 2 resumes from it,
+ * bit-identical to an uninterrupted run.  gamma/beta NULL: gamma0 = 0,
+ * beta = 1. */
+gda_status gda_set_state(gda_ctx* ctx, const float* psi, const float* gamma, const float* beta,
+                         int32_t R, int64_t step);
+
+/* Copies out the energy trace of the last run (host arrays of capacity cap):
+ * step index, best tracking energy and its restart.  *count receives the
+ * number of entries recorded (may exceed cap).  Synchronises. */
+gda_status gda_trace(gda_ctx* ctx, int64_t* step, double* E, int32_t* r, int32_t cap, int32_t* count);
+
+/* The coupling product alone (the GEMM of Eq. 2's sum over j != i):
+ * Y = J0 X for R restarts, with J0 = J minus its diagonal, through the
+ * FP32 (prec = GDA_FP32) or tensor-core BF16 (GDA_BF16) path.  X, Y: host
+ * arrays in the psi layout of gda_get_state.  Replaces the context's state
+ * (a following gda_run must start with init_mode 0 or 1).  Synchronises. */
+gda_status gda_coupling(gda_ctx* ctx, int32_t prec, int32_t R, const float* X, float* Y);
+
+/* Number of kernels the library launched on this context since creation. */
+int64_t gda_kernel_launches(const gda_ctx* ctx);
+
+/* Last error message of this context ("" if none). */
+const char* gda_last_error(const gda_ctx* ctx);
+
+/* Static description of a status code. */
+const char* gda_status_string(gda_status s);
+
+/* Frees the context and all its device memory (NULL is a no-op). */
+void gda_destroy(gda_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GDA_H */

@@ -1,0 +1,663 @@
+// C ABI of the GD solver (include/gda.h): context, device memory, the step
+// loop and the energy / argmin calls.  The arithmetic runs in the kernels of
+// step_simt.cu, step_tc.cu and energy.cu; this file only orders launches.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/gda.h"
+#include "gda_internal.h"
+#include "kernels.h"
+
+using namespace gda;
+
+namespace {
+
+constexpr int kTraceCap = 1 << 16;
+
+size_t round_up(size_t x, size_t m) { return (x + m - 1) / m * m; }
+
+}  // namespace
+
+struct gda_ctx {
+  int dev = 0;
+  int N = 0, Np = 0, model = 0, cplx = 0;
+  cudaStream_t stream = nullptr;
+  bool tc_ok = false;
+  // instance
+  double* J64 = nullptr;  // [Np][Np], diagonal kept
+  float* J32 = nullptr;   // [Np][Np], diagonal removed
+  __nv_bfloat16* J16 = nullptr;
+  int* Jint = nullptr;
+  double* g64 = nullptr;  // [Np]
+  float* g32 = nullptr;   // [Np]
+  float* h1 = nullptr;    // [Np]
+  bool int_exact = false;
+  double diag = 0.0;      // -sum_i J_ii
+  // instance checks
+  int* d_flags = nullptr;
+  unsigned long long* d_maxabs = nullptr;
+  double* d_diag = nullptr;
+  // state
+  int R = 0, C = 0, Cp = 0, Rp = 0, Rcap_cols = 0, MT = 0;
+  float* psi[2] = {nullptr, nullptr};
+  float* stg[2] = {nullptr, nullptr};
+  float* acc = nullptr;
+  float* S32 = nullptr;
+  float* gam = nullptr;
+  float* gstg = nullptr;
+  float* gacc = nullptr;
+  float* beta[2] = {nullptr, nullptr};
+  float* rho[2] = {nullptr, nullptr};
+  float* epart = nullptr;
+  __nv_bfloat16* ops = nullptr;  // [3][Cp][Np]: operand ping-pong + projected spins
+  double* S64 = nullptr;
+  int* Sint = nullptr;
+  double* part64 = nullptr;
+  long long* partint = nullptr;
+  double* E64 = nullptr;
+  double* bestE = nullptr;
+  int* bestR = nullptr;
+  signed char* cfg8 = nullptr;
+  double* cfgth = nullptr;
+  long long* t_step = nullptr;
+  double* t_E = nullptr;
+  int* t_r = nullptr;
+  int* t_count = nullptr;
+  int* err = nullptr;
+  TcPlan* plan = nullptr;
+  int cur = 0, bcur = 0, rcur = 0, opcur = 0;
+  long long step = 0;
+  bool have_state = false;
+  long long launches = 0;
+  std::string msg;
+};
+
+namespace {
+
+gda_status fail(gda_ctx* c, gda_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (c) c->msg = buf;
+  return s;
+}
+
+gda_status cuda_fail(gda_ctx* c, cudaError_t e, const char* what) {
+  cudaGetLastError();
+  return fail(c, e == cudaErrorMemoryAllocation ? GDA_ERR_OOM : GDA_ERR_CUDA, "%s: %s", what,
+              cudaGetErrorString(e));
+}
+
+#define CK(expr)                                            \
+  do {                                                      \
+    cudaError_t e_ = (expr);                                \
+    if (e_ != cudaSuccess) return cuda_fail(c, e_, #expr); \
+  } while (0)
+
+#define LK(expr)                                            \
+  do {                                                      \
+    cudaError_t e_ = (expr);                                \
+    ++c->launches;                                          \
+    if (e_ != cudaSuccess) return cuda_fail(c, e_, #expr); \
+  } while (0)
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t n) {
+  *p = nullptr;
+  if (n == 0) return cudaSuccess;
+  return cudaMalloc(reinterpret_cast<void**>(p), n * sizeof(T));
+}
+
+template <typename T>
+void dfree(T*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+void free_state(gda_ctx* c) {
+  for (int k = 0; k < 2; ++k) {
+    dfree(c->psi[k]);
+    dfree(c->stg[k]);
+    dfree(c->beta[k]);
+    dfree(c->rho[k]);
+  }
+  dfree(c->acc); dfree(c->S32); dfree(c->gam); dfree(c->gstg); dfree(c->gacc); dfree(c->epart);
+  dfree(c->ops); dfree(c->S64); dfree(c->Sint); dfree(c->part64); dfree(c->partint); dfree(c->E64);
+  if (c->plan) tc_plan_destroy(c->plan);
+  c->plan = nullptr;
+  c->R = c->C = c->Cp = c->Rp = c->Rcap_cols = 0;
+  c->have_state = false;
+}
+
+// Allocates (or keeps) the state for R restarts; padding stays zero.
+gda_status ensure_state(gda_ctx* c, int R) {
+  const int C = c->cplx ? 2 * R : R;
+  if (c->Rcap_cols >= C && c->psi[0]) {
+    c->R = R;
+    c->C = C;
+    return GDA_OK;
+  }
+  free_state(c);
+  const size_t Cp = round_up(C, 256), Np = c->Np;
+  const size_t Rp = round_up(R, 256);
+  const size_t MT = (c->N + 63) / 64;
+  const size_t cn = Cp * Np, rn = Rp * Np;
+  for (int k = 0; k < 2; ++k) {
+    CK(dalloc(&c->psi[k], cn));
+    CK(dalloc(&c->stg[k], cn));
+    CK(dalloc(&c->beta[k], Rp));
+    CK(dalloc(&c->rho[k], MT * Rp));
+  }
+  CK(dalloc(&c->acc, cn));
+  CK(dalloc(&c->S32, cn));
+  CK(dalloc(&c->gam, rn));
+  CK(dalloc(&c->gstg, rn));
+  CK(dalloc(&c->gacc, rn));
+  CK(dalloc(&c->epart, MT * Rp));
+  CK(dalloc(&c->S64, cn));
+  CK(dalloc(&c->part64, MT * Rp));
+  CK(dalloc(&c->E64, Rp));
+  if (c->int_exact || c->model == GDA_ISING) {
+    CK(dalloc(&c->Sint, cn));
+    CK(dalloc(&c->partint, MT * Rp));
+  }
+  float* zf[] = {c->psi[0], c->psi[1], c->stg[0], c->stg[1], c->acc, c->S32};
+  for (float* p : zf) CK(cudaMemsetAsync(p, 0, cn * sizeof(float), c->stream));
+  CK(cudaMemsetAsync(c->S64, 0, cn * sizeof(double), c->stream));
+  if (c->Sint) CK(cudaMemsetAsync(c->Sint, 0, cn * sizeof(int), c->stream));
+  CK(cudaMemsetAsync(c->gam, 0, rn * sizeof(float), c->stream));
+  CK(cudaMemsetAsync(c->gstg, 0, rn * sizeof(float), c->stream));
+  CK(cudaMemsetAsync(c->gacc, 0, rn * sizeof(float), c->stream));
+  if (c->tc_ok) {
+    CK(dalloc(&c->ops, 3 * cn));
+    CK(cudaMemsetAsync(c->ops, 0, 3 * cn * sizeof(__nv_bfloat16), c->stream));
+    CK(tc_plan_create(&c->plan, c->J16, int(Np), c->ops, 3, int(Cp)));
+  }
+  c->R = R;
+  c->C = C;
+  c->Cp = int(Cp);
+  c->Rp = int(Rp);
+  c->MT = int(MT);
+  c->Rcap_cols = int(Cp);
+  return GDA_OK;
+}
+
+// Uploads J (N x N, row-major) and g into the padded FP64 copies, checks the
+// instance on the device and derives the coupling operands.
+gda_status load_instance(gda_ctx* c, const double* J, const double* g, cudaMemcpyKind kind) {
+  const size_t Np = c->Np, N = c->N;
+  CK(cudaMemsetAsync(c->J64, 0, Np * Np * sizeof(double), c->stream));
+  CK(cudaMemcpy2DAsync(c->J64, Np * sizeof(double), J, N * sizeof(double), N * sizeof(double), N, kind, c->stream));
+  CK(cudaMemsetAsync(c->g64, 0, Np * sizeof(double), c->stream));
+  if (g) CK(cudaMemcpyAsync(c->g64, g, N * sizeof(double), kind, c->stream));
+  CK(cudaMemsetAsync(c->d_flags, 0, sizeof(int), c->stream));
+  CK(cudaMemsetAsync(c->d_maxabs, 0, sizeof(unsigned long long), c->stream));
+  LK(launch_check_instance(c->J64, c->g64, c->N, c->Np, c->d_flags, c->d_maxabs, c->d_diag, c->stream));
+  int flags = 0;
+  unsigned long long mbits = 0;
+  CK(cudaMemcpyAsync(&flags, c->d_flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(&mbits, c->d_maxabs, sizeof(mbits), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(&c->diag, c->d_diag, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (flags & 1) return fail(c, GDA_ERR_INVALID, "J has a non-finite entry");
+  if (flags & 2) return fail(c, GDA_ERR_INVALID, "J is not symmetric");
+  if (flags & 8) return fail(c, GDA_ERR_INVALID, "g has a non-finite entry");
+  double maxabs;
+  std::memcpy(&maxabs, &mbits, sizeof(maxabs));
+  const bool was_int = c->int_exact;
+  c->int_exact = c->model == GDA_ISING && !(flags & 4) && !(flags & 16) && maxabs * double(N) < 2147483647.0;
+  if (c->int_exact && !c->Jint) CK(dalloc(&c->Jint, Np * Np));
+  if (c->int_exact && !was_int && c->psi[0] && !c->Sint) {
+    CK(dalloc(&c->Sint, size_t(c->Cp) * Np));
+    CK(cudaMemsetAsync(c->Sint, 0, size_t(c->Cp) * Np * sizeof(int), c->stream));
+    CK(dalloc(&c->partint, size_t(c->MT) * c->Rp));
+  }
+  LK(launch_prepare_J(c->J64, c->Np, c->J32, c->J16, c->int_exact ? c->Jint : nullptr, c->stream));
+  return GDA_OK;
+}
+
+bool finite(double x) { return std::isfinite(x); }
+
+gda_status check_params(gda_ctx* c, const gda_params* p) {
+  if (!p) return fail(c, GDA_ERR_INVALID, "params is NULL");
+  if (p->integ != GDA_EULER && p->integ != GDA_RK4) return fail(c, GDA_ERR_INVALID, "unknown integrator %d", p->integ);
+  if (p->prec != GDA_FP32 && p->prec != GDA_BF16) return fail(c, GDA_ERR_INVALID, "unknown precision %d", p->prec);
+  const double v[] = {p->dt, p->eps, p->rho_th, p->gamma0, p->beta0, p->eps_hat, p->noise_D, p->init_amp};
+  for (double x : v)
+    if (!finite(x)) return fail(c, GDA_ERR_INVALID, "non-finite parameter");
+  if (!(p->dt > 0)) return fail(c, GDA_ERR_INVALID, "dt must be > 0");
+  if (!(p->rho_th > 0)) return fail(c, GDA_ERR_INVALID, "rho_th must be > 0");
+  if (p->noise_D < 0) return fail(c, GDA_ERR_INVALID, "noise_D must be >= 0");
+  if (p->init_mode < 0 || p->init_mode > 2) return fail(c, GDA_ERR_INVALID, "init_mode must be 0, 1 or 2");
+  if (p->energy_every < 0) return fail(c, GDA_ERR_INVALID, "energy_every must be >= 0");
+  if (p->prec == GDA_BF16 && !c->tc_ok)
+    return fail(c, GDA_ERR_UNSUPPORTED, "BF16 tensor-core path needs an sm_103 device");
+  return GDA_OK;
+}
+
+StepArgs base_args(gda_ctx* c, const gda_params* p, bool tc) {
+  StepArgs a{};
+  a.N = c->N; a.Np = c->Np; a.C = c->C; a.R = c->R; a.Cp = c->Cp; a.Rp = c->Rp;
+  a.cplx = c->cplx;
+  a.mt_count = tc ? tc_mtiles(c->N) : simt_mtiles(c->N);
+  a.dt = float(p->dt); a.eps = float(p->eps); a.rho_th = float(p->rho_th); a.eps_hat = float(p->eps_hat);
+  a.noise_D = float(p->noise_D);
+  a.noise_decay = p->noise_decay ? 1 : 0;
+  a.seed = p->seed;
+  a.acc = c->acc; a.gam = c->gam; a.gstg = c->gstg; a.gacc = c->gacc;
+  a.h1 = c->h1;
+  a.g = c->g32;
+  a.e_part = c->epart;
+  a.err = c->err;
+  return a;
+}
+
+gda_status launch_step(gda_ctx* c, const StepArgs& a, bool tc, const float* operand32, int op_buf) {
+  if (tc) {
+    LK(launch_step_tc(c->plan, a, op_buf, c->stream));
+  } else {
+    LK(launch_step_simt(a, c->J32, operand32, c->stream));
+  }
+  return GDA_OK;
+}
+
+// One tracking evaluation of the projected spins of psi[cur].
+gda_status track(gda_ctx* c, const gda_params* p, bool tc, long long step) {
+  StepArgs a = base_args(c, p, tc);
+  a.mode = M_ENERGY;
+  a.psi_n = c->psi[c->cur];
+  a.beta_in = c->beta[c->bcur];
+  if (tc) {
+    LK(launch_project_bf16(c->psi[c->cur], c->ops + size_t(2) * c->Cp * c->Np, c->N, c->Np, c->R, c->cplx,
+                           c->stream));
+  } else {
+    LK(launch_project_f32(c->psi[c->cur], c->S32, c->N, c->Np, c->R, c->cplx, c->stream));
+  }
+  gda_status s = launch_step(c, a, tc, c->S32, 2);
+  if (s != GDA_OK) return s;
+  LK(launch_track_reduce(c->epart, a.mt_count, c->R, c->Rp, c->diag, step, c->t_step, c->t_E, c->t_r, kTraceCap,
+                         c->t_count, c->stream));
+  return GDA_OK;
+}
+
+gda_status compute_energies(gda_ctx* c) {
+  if (!c->have_state) return fail(c, GDA_ERR_STATE, "no state: call gda_run or gda_set_state first");
+  if (c->int_exact) {
+    LK(launch_energy_int(c->psi[c->cur], c->Jint, c->Sint, c->partint, c->E64, c->N, c->Np, c->R, c->Rp, c->C,
+                         c->stream));
+  } else {
+    LK(launch_energy64(c->psi[c->cur], c->J64, c->g64, c->S64, c->part64, c->E64, c->N, c->Np, c->R, c->Rp, c->C,
+                       c->cplx, c->stream));
+  }
+  return GDA_OK;
+}
+
+gda_status check_err(gda_ctx* c) {
+  int e = 0;
+  CK(cudaMemcpyAsync(&e, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (e) {
+    CK(cudaMemsetAsync(c->err, 0, sizeof(int), c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (e & E_TIMEOUT) return fail(c, GDA_ERR_TIMEOUT, "a device-side wait timed out");
+    return fail(c, GDA_ERR_DIVERGED, "non-finite or overflowing amplitude");
+  }
+  return GDA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void gda_default_params(gda_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->integ = GDA_EULER;
+  p->prec = GDA_FP32;
+  p->dt = 0.01;
+  p->eps = 0.1;
+  p->rho_th = 1.0;
+  p->gamma0 = 0.0;
+  p->beta0 = 1.0;
+  p->eps_hat = 0.0;
+  p->noise_D = 0.0;
+  p->noise_decay = 0;
+  p->energy_every = 0;
+  p->seed = 0;
+  p->init_mode = 1;
+  p->init_amp = 1e-3;
+}
+
+const char* gda_status_string(gda_status s) {
+  switch (s) {
+    case GDA_OK: return "ok";
+    case GDA_ERR_INVALID: return "invalid argument";
+    case GDA_ERR_CUDA: return "CUDA error";
+    case GDA_ERR_OOM: return "out of device memory";
+    case GDA_ERR_DIVERGED: return "amplitudes diverged";
+    case GDA_ERR_TIMEOUT: return "device wait timed out";
+    case GDA_ERR_UNSUPPORTED: return "unsupported on this device";
+    case GDA_ERR_STATE: return "call out of order";
+  }
+  return "unknown status";
+}
+
+const char* gda_last_error(const gda_ctx* c) { return c ? c->msg.c_str() : "NULL context"; }
+
+int64_t gda_kernel_launches(const gda_ctx* c) { return c ? c->launches : 0; }
+
+void gda_destroy(gda_ctx* c) {
+  if (!c) return;
+  free_state(c);
+  dfree(c->J64); dfree(c->J32); dfree(c->J16); dfree(c->Jint); dfree(c->g64); dfree(c->g32); dfree(c->h1);
+  dfree(c->d_flags); dfree(c->d_maxabs); dfree(c->d_diag);
+  dfree(c->bestE); dfree(c->bestR); dfree(c->cfg8); dfree(c->cfgth);
+  dfree(c->t_step); dfree(c->t_E); dfree(c->t_r); dfree(c->t_count); dfree(c->err);
+  delete c;
+}
+
+static gda_status create_impl(const double* J, const double* g, int32_t N, int32_t model, gda_ctx** out,
+                              cudaMemcpyKind kind) {
+  if (!out) return GDA_ERR_INVALID;
+  *out = nullptr;
+  if (!J || N < 1 || N > 65536 || (model != GDA_ISING && model != GDA_XY)) return GDA_ERR_INVALID;
+  if (kind == cudaMemcpyHostToDevice) {
+    // host-side screening of the cheap conditions before any allocation
+    for (int64_t k = 0; k < int64_t(N) * N; ++k)
+      if (!std::isfinite(J[k])) return GDA_ERR_INVALID;
+    for (int32_t i = 0; i < N; ++i)
+      for (int32_t j = i + 1; j < N; ++j)
+        if (J[int64_t(i) * N + j] != J[int64_t(j) * N + i]) return GDA_ERR_INVALID;
+    if (g)
+      for (int32_t i = 0; i < N; ++i)
+        if (!std::isfinite(g[i])) return GDA_ERR_INVALID;
+  }
+  gda_ctx* c = new gda_ctx();
+  c->N = N;
+  c->Np = int(round_up(N, 128));
+  c->model = model;
+  c->cplx = model == GDA_XY;
+  if (cudaGetDevice(&c->dev) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return GDA_ERR_CUDA;
+  }
+  c->tc_ok = tc_supported(c->dev);
+  const size_t Np = c->Np;
+  gda_status st = GDA_OK;
+  auto step = [&](cudaError_t e) {
+    if (st == GDA_OK && e != cudaSuccess) st = cuda_fail(c, e, "gda_create allocation");
+  };
+  step(dalloc(&c->J64, Np * Np));
+  step(dalloc(&c->J32, Np * Np));
+  if (c->tc_ok) step(dalloc(&c->J16, Np * Np));
+  step(dalloc(&c->g64, Np));
+  step(dalloc(&c->g32, Np));
+  step(dalloc(&c->h1, Np));
+  step(dalloc(&c->d_flags, 1));
+  step(dalloc(&c->d_maxabs, 1));
+  step(dalloc(&c->d_diag, 1));
+  step(dalloc(&c->bestE, 1));
+  step(dalloc(&c->bestR, 1));
+  step(dalloc(&c->cfg8, Np));
+  step(dalloc(&c->cfgth, Np));
+  step(dalloc(&c->t_step, kTraceCap));
+  step(dalloc(&c->t_E, kTraceCap));
+  step(dalloc(&c->t_r, kTraceCap));
+  step(dalloc(&c->t_count, 1));
+  step(dalloc(&c->err, 1));
+  if (st == GDA_OK) step(cudaMemset(c->err, 0, sizeof(int)));
+  if (st == GDA_OK) step(cudaMemset(c->t_count, 0, sizeof(int)));
+  if (st == GDA_OK) step(cudaMemset(c->h1, 0, Np * sizeof(float)));
+  if (st == GDA_OK) step(cudaMemset(c->g32, 0, Np * sizeof(float)));
+  if (st == GDA_OK) st = load_instance(c, J, g, kind);
+  if (st != GDA_OK) {
+    gda_destroy(c);
+    return st;
+  }
+  *out = c;
+  return GDA_OK;
+}
+
+gda_status gda_create(const double* J, const double* g, int32_t N, int32_t model, gda_ctx** out) {
+  return create_impl(J, g, N, model, out, cudaMemcpyHostToDevice);
+}
+
+static gda_status load_common(gda_ctx* c, const double* J, const double* g, cudaMemcpyKind kind) {
+  if (!c) return GDA_ERR_INVALID;
+  if (!J) return fail(c, GDA_ERR_INVALID, "J is NULL");
+  gda_status s = load_instance(c, J, g, kind);
+  if (s == GDA_OK) c->have_state = false;
+  return s;
+}
+
+gda_status gda_load(gda_ctx* c, const double* J, const double* g) {
+  return load_common(c, J, g, cudaMemcpyHostToDevice);
+}
+
+gda_status gda_load_dev(gda_ctx* c, const double* J_dev, const double* g_dev) {
+  return load_common(c, J_dev, g_dev, cudaMemcpyDeviceToDevice);
+}
+
+gda_status gda_set_stream(gda_ctx* c, void* stream) {
+  if (!c) return GDA_ERR_INVALID;
+  c->stream = static_cast<cudaStream_t>(stream);
+  return GDA_OK;
+}
+
+gda_status gda_run(gda_ctx* c, const gda_params* p, int32_t R, int64_t steps) {
+  if (!c) return GDA_ERR_INVALID;
+  gda_status s = check_params(c, p);
+  if (s != GDA_OK) return s;
+  if (R < 1) return fail(c, GDA_ERR_INVALID, "R must be >= 1");
+  if (steps < 0) return fail(c, GDA_ERR_INVALID, "steps must be >= 0");
+  if (size_t(c->cplx ? 2 : 1) * size_t(R) > size_t(1) << 24) return fail(c, GDA_ERR_INVALID, "R too large");
+  const bool tc = p->prec == GDA_BF16;
+  if (p->init_mode == 2) {
+    if (!c->have_state || c->R != R) return fail(c, GDA_ERR_STATE, "init_mode 2 needs a state with the same R");
+  } else {
+    s = ensure_state(c, R);
+    if (s != GDA_OK) return s;
+    LK(launch_init_state(c->psi[0], c->gam, c->beta[0], c->N, c->Np, R, c->cplx, p->init_mode, float(p->init_amp),
+                         float(p->gamma0), float(p->beta0), p->seed, c->stream));
+    c->cur = 0;
+    c->bcur = 0;
+    c->step = 0;
+    c->have_state = true;
+  }
+  CK(cudaMemsetAsync(c->t_count, 0, sizeof(int), c->stream));
+  LK(launch_fill_h1(c->g64, c->h1, c->N, float(std::sqrt(p->rho_th)), c->stream));
+  // field in FP32 for the tracking energy
+  LK(launch_fill_h1(c->g64, c->g32, c->N, -1.0f, c->stream));
+  const size_t cn = size_t(c->Cp) * c->Np;
+  c->opcur = 0;
+  if (tc) LK(launch_to_bf16(c->psi[c->cur], c->ops, cn, c->stream));
+  const bool decay = p->noise_D != 0.0 && p->noise_decay;
+  c->rcur = 0;
+  if (decay) LK(launch_rho_partials(tc, c->psi[c->cur], c->N, c->Np, c->R, c->Rp, c->cplx, c->rho[0], c->stream));
+
+  StepArgs base = base_args(c, p, tc);
+  const size_t opsz = cn;
+  for (int64_t k = 0; k < steps; ++k) {
+    const long long n = c->step + k;
+    StepArgs a = base;
+    a.step = static_cast<unsigned int>(n);
+    a.beta_in = c->beta[c->bcur];
+    a.beta_out = c->beta[c->bcur ^ 1];
+    a.rho_in = c->rho[c->rcur];
+    a.rho_out = decay ? c->rho[c->rcur ^ 1] : nullptr;
+    if (p->integ == GDA_EULER) {
+      a.mode = M_EULER;
+      a.psi_n = c->psi[c->cur];
+      a.xs = c->psi[c->cur];
+      a.psi_out = c->psi[c->cur ^ 1];
+      a.op_out = tc ? c->ops + (c->opcur ^ 1) * opsz : nullptr;
+      s = launch_step(c, a, tc, c->psi[c->cur], c->opcur);
+      if (s != GDA_OK) return s;
+      c->cur ^= 1;
+      c->opcur ^= 1;
+    } else {
+      const float* xin[4] = {c->psi[c->cur], c->stg[0], c->stg[1], c->stg[0]};
+      float* xout[3] = {c->stg[0], c->stg[1], c->stg[0]};
+      for (int st = 0; st < 4; ++st) {
+        a.mode = M_RK1 + st;
+        a.psi_n = c->psi[c->cur];
+        a.xs = xin[st];
+        a.xs_next = st < 3 ? xout[st] : nullptr;
+        a.psi_out = c->psi[c->cur];
+        const int in_buf = c->opcur ^ (st & 1);
+        a.op_out = tc ? c->ops + (in_buf ^ 1) * opsz : nullptr;
+        s = launch_step(c, a, tc, xin[st], in_buf);
+        if (s != GDA_OK) return s;
+      }
+    }
+    c->bcur ^= 1;
+    if (decay) c->rcur ^= 1;
+    if (p->energy_every > 0 && (k + 1) % p->energy_every == 0) {
+      s = track(c, p, tc, n + 1);
+      if (s != GDA_OK) return s;
+    }
+  }
+  c->step += steps;
+  return GDA_OK;
+}
+
+gda_status gda_sync(gda_ctx* c) {
+  if (!c) return GDA_ERR_INVALID;
+  CK(cudaStreamSynchronize(c->stream));
+  return check_err(c);
+}
+
+gda_status gda_energy_dev(gda_ctx* c, double* E_dev) {
+  if (!c) return GDA_ERR_INVALID;
+  if (!E_dev) return fail(c, GDA_ERR_INVALID, "E_dev is NULL");
+  gda_status s = compute_energies(c);
+  if (s != GDA_OK) return s;
+  CK(cudaMemcpyAsync(E_dev, c->E64, size_t(c->R) * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  return GDA_OK;
+}
+
+gda_status gda_energy(gda_ctx* c, double* E) {
+  if (!c) return GDA_ERR_INVALID;
+  if (!E) return fail(c, GDA_ERR_INVALID, "E is NULL");
+  gda_status s = compute_energies(c);
+  if (s != GDA_OK) return s;
+  CK(cudaMemcpyAsync(E, c->E64, size_t(c->R) * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  return check_err(c);
+}
+
+gda_status gda_best(gda_ctx* c, double* E, int32_t* r, void* cfg) {
+  if (!c) return GDA_ERR_INVALID;
+  gda_status s = compute_energies(c);
+  if (s != GDA_OK) return s;
+  LK(launch_argmin(c->E64, c->R, c->bestE, c->bestR, c->stream));
+  double e = 0.0;
+  int rr = 0;
+  CK(cudaMemcpyAsync(&e, c->bestE, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(&rr, c->bestR, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  if (cfg) {
+    LK(launch_best_cfg(c->psi[c->cur], c->bestR, c->N, c->Np, c->cplx, c->cfg8, c->cfgth, c->stream));
+    if (c->cplx)
+      CK(cudaMemcpyAsync(cfg, c->cfgth, size_t(c->N) * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    else
+      CK(cudaMemcpyAsync(cfg, c->cfg8, size_t(c->N), cudaMemcpyDeviceToHost, c->stream));
+  }
+  s = check_err(c);
+  if (s != GDA_OK) return s;
+  if (E) *E = e;
+  if (r) *r = rr;
+  return GDA_OK;
+}
+
+gda_status gda_get_state(gda_ctx* c, float* psi, float* gamma, float* beta, int64_t* step) {
+  if (!c) return GDA_ERR_INVALID;
+  if (!c->have_state) return fail(c, GDA_ERR_STATE, "no state");
+  const size_t rn = size_t(c->R) * c->N, W = c->cplx ? 2 : 1;
+  // stage in the RK buffers (scratch between runs), then one copy each
+  float* hp = c->stg[1];
+  float* hg = c->gstg;
+  float* hb = c->beta[c->bcur ^ 1];
+  LK(launch_pack_state(c->psi[c->cur], c->gam, c->beta[c->bcur], c->N, c->Np, c->R, c->cplx, hp, hg, hb, c->stream));
+  if (psi) CK(cudaMemcpyAsync(psi, hp, rn * W * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+  if (gamma) CK(cudaMemcpyAsync(gamma, hg, rn * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+  if (beta) CK(cudaMemcpyAsync(beta, hb, size_t(c->R) * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+  gda_status s = check_err(c);
+  if (s != GDA_OK) return s;
+  if (step) *step = c->step;
+  return GDA_OK;
+}
+
+gda_status gda_set_state(gda_ctx* c, const float* psi, const float* gamma, const float* beta, int32_t R,
+                         int64_t step) {
+  if (!c) return GDA_ERR_INVALID;
+  if (!psi || R < 1 || step < 0) return fail(c, GDA_ERR_INVALID, "psi NULL, R < 1 or step < 0");
+  gda_status s = ensure_state(c, R);
+  if (s != GDA_OK) return s;
+  const size_t rn = size_t(R) * c->N, W = c->cplx ? 2 : 1;
+  float* hp = c->stg[1];
+  float* hg = c->gstg;
+  float* hb = c->beta[1];
+  CK(cudaMemcpyAsync(hp, psi, rn * W * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+  if (gamma) CK(cudaMemcpyAsync(hg, gamma, rn * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+  if (beta) CK(cudaMemcpyAsync(hb, beta, size_t(R) * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+  LK(launch_unpack_state(c->psi[0], c->gam, c->beta[0], c->N, c->Np, R, c->cplx, hp, gamma ? hg : nullptr,
+                         beta ? hb : nullptr, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->cur = 0;
+  c->bcur = 0;
+  c->step = step;
+  c->have_state = true;
+  return GDA_OK;
+}
+
+gda_status gda_trace(gda_ctx* c, int64_t* step, double* E, int32_t* r, int32_t cap, int32_t* count) {
+  if (!c) return GDA_ERR_INVALID;
+  int n = 0;
+  CK(cudaMemcpyAsync(&n, c->t_count, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  const int m = std::min(std::min(n, cap), kTraceCap);
+  if (m > 0) {
+    if (step) CK(cudaMemcpyAsync(step, c->t_step, m * sizeof(long long), cudaMemcpyDeviceToHost, c->stream));
+    if (E) CK(cudaMemcpyAsync(E, c->t_E, m * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if (r) CK(cudaMemcpyAsync(r, c->t_r, m * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  }
+  gda_status s = check_err(c);
+  if (s != GDA_OK) return s;
+  if (count) *count = n;
+  return GDA_OK;
+}
+
+gda_status gda_coupling(gda_ctx* c, int32_t prec, int32_t R, const float* X, float* Y) {
+  if (!c) return GDA_ERR_INVALID;
+  if (!X || !Y || R < 1) return fail(c, GDA_ERR_INVALID, "X or Y NULL, or R < 1");
+  if (prec != GDA_FP32 && prec != GDA_BF16) return fail(c, GDA_ERR_INVALID, "unknown precision");
+  if (prec == GDA_BF16 && !c->tc_ok) return fail(c, GDA_ERR_UNSUPPORTED, "BF16 path needs an sm_103 device");
+  gda_status s = gda_set_state(c, X, nullptr, nullptr, R, 0);
+  if (s != GDA_OK) return s;
+  const bool tc = prec == GDA_BF16;
+  gda_params p;
+  gda_default_params(&p);
+  StepArgs a = base_args(c, &p, tc);
+  a.mode = M_RAW;
+  a.psi_n = c->psi[0];
+  a.xs = c->psi[0];
+  a.psi_out = c->stg[0];
+  a.beta_in = c->beta[0];
+  if (tc) LK(launch_to_bf16(c->psi[0], c->ops, size_t(c->Cp) * c->Np, c->stream));
+  s = launch_step(c, a, tc, c->psi[0], 0);
+  if (s != GDA_OK) return s;
+  const size_t rn = size_t(R) * c->N, W = c->cplx ? 2 : 1;
+  LK(launch_pack_state(c->stg[0], c->gam, c->beta[0], c->N, c->Np, R, c->cplx, c->stg[1], nullptr, nullptr,
+                       c->stream));
+  CK(cudaMemcpyAsync(Y, c->stg[1], rn * W * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+  return check_err(c);
+}
+
+}  // extern "C"

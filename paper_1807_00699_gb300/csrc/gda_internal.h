@@ -1,0 +1,80 @@
+// Internal types shared by the host runtime and the kernels.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace gda {
+
+// What one launch of a step kernel computes in its epilogue.
+enum Mode : int {
+  M_EULER = 0,   // forward Euler step (plus noise)
+  M_RK1 = 1,     // RK4 stages 1..4 (stage 4 completes the step, plus noise)
+  M_RK2 = 2,
+  M_RK3 = 3,
+  M_RK4 = 4,
+  M_ENERGY = 5,  // per-restart Eq. (1) partial energies of the projected spins
+  M_RAW = 6,     // writes Y = J0 X itself (the coupling product alone)
+};
+
+// |psi|^2 with a fixed rounding sequence, so every kernel that forms a
+// density gets the same bits.
+__host__ __device__ __forceinline__ float density(float re, float im) {
+#ifdef __CUDA_ARCH__
+  return __fadd_rn(__fmul_rn(re, re), __fmul_rn(im, im));
+#else
+  return re * re + im * im;
+#endif
+}
+
+// Device error bits (OR-ed into a flag the host reads at sync points).
+enum DevErr : int { E_DIVERGED = 1, E_TIMEOUT = 2 };
+
+// Layout: spins are padded to Np (a multiple of 128) and columns to Cp (a
+// multiple of 256).  A "column" c is one real amplitude series: c = r for
+// Ising, c = 2r (real part) and 2r+1 (imaginary part) for XY.  Column-major
+// state: x[c * Np + i].  Per-restart arrays: y[r * Np + i].  Padding is zero
+// and never written.
+struct StepArgs {
+  int N, Np, C, R, Cp, Rp;
+  int mode;
+  int cplx;
+  int mt_count;          // M tiles of the launching kernel (rho / energy partials)
+  float dt, eps, rho_th, eps_hat;
+  float noise_D;
+  int noise_decay;
+  unsigned long long seed;
+  unsigned int step;     // global step index n of this transition n -> n+1
+  const float* psi_n;    // psi^n, FP32 [Cp][Np]
+  float* psi_out;        // Euler: psi^{n+1}; RK stage 4: psi^n updated in place
+  const float* xs;       // RK stage input X_s (stage 1: psi_n)
+  float* xs_next;        // RK stages 1-3: X_{s+1}
+  float* acc;            // RK accumulator of psi increments [Cp][Np]
+  float* gam;            // gamma^n [Rp][Np] (updated in place at the end of a step)
+  float* gstg;           // RK stage gains [Rp][Np]
+  float* gacc;           // RK accumulator of gamma increments [Rp][Np]
+  __nv_bfloat16* op_out; // BF16 copy of the next GEMM operand, or nullptr
+  const float* h1;       // drive h_1i = -g_i sqrt(rho_th), [Np]
+  const float* beta_in;  // beta^n [Rp]
+  float* beta_out;       // beta^{n+1} [Rp]
+  const float* rho_in;   // [mt_count][Rp] partial sums of |psi^n|^2 over spins
+  float* rho_out;        // [mt_count][Rp] partial sums of |psi^{n+1}|^2
+  const float* g;        // field g_i [Np] (energy mode)
+  float* e_part;         // [mt_count][Rp] partial energies (energy mode)
+  int* err;
+};
+
+// Launchers (return cudaGetLastError() of the launch).
+cudaError_t launch_step_simt(const StepArgs& a, const float* J32, const float* operand, cudaStream_t s);
+int simt_mtiles(int N);
+
+struct TcPlan;  // opaque plan holding the tensor maps of one context
+cudaError_t tc_plan_create(TcPlan** plan, const __nv_bfloat16* J16, int Np,
+                           const __nv_bfloat16* ops, int n_op_bufs, int Cp);
+void tc_plan_destroy(TcPlan* plan);
+cudaError_t launch_step_tc(const TcPlan* plan, const StepArgs& a, int op_buf, cudaStream_t s);
+int tc_mtiles(int N);
+bool tc_supported(int device);
+
+}  // namespace gda

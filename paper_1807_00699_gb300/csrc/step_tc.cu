@@ -1,0 +1,377 @@
+// Tensor-core GD step for sm_103a: Y = J0 X with tcgen05.mma (BF16 operands,
+// FP32 accumulator in tensor memory), both operands staged in shared memory by
+// TMA (cp.async.bulk.tensor, 128-byte swizzle, no multicast), fused with the
+// step epilogue of Eqs. (2), (5), (6).
+//
+// One CTA computes one 128 x BN tile of Y (spins x columns).  Warp roles:
+//   warp 0        TMA producer (one elected lane), STAGES-deep ring
+//   warp 1        TMEM allocator and MMA issuer (one elected lane)
+//   warps 2..9    epilogue: warp w reads TMEM lane quarter (w % 4), half of
+//                 the columns each, and runs the per-element update.
+// Every mbarrier wait is bounded by a clock budget; on expiry the CTA records
+// E_TIMEOUT, stops issuing work, drains what it issued and frees its TMEM.
+#include <cuda.h>
+
+#include <cstdio>
+
+#include "epilogue.cuh"
+
+namespace gda {
+
+namespace {
+
+constexpr int BM = 128;
+constexpr int BK = 64;  // 64 BF16 = 128 bytes: one swizzle row
+constexpr int NTHREADS = 320;
+constexpr long long kWaitCycles = 4000000000LL;  // about two seconds
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for the phase with the given parity to complete.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  if (mbar_try(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try(bar, parity)) {
+    if (clock64() - t0 > kWaitCycles) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot), "r"(ncols) : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
+// 128 bytes, 8-row core-matrix groups 1024 bytes apart (SBO), descriptor
+// version 1 (sm_100 family).
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+  uint64_t d = static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);
+  d |= static_cast<uint64_t>(1) << 16;
+  d |= static_cast<uint64_t>(1024 >> 4) << 32;
+  d |= static_cast<uint64_t>(1) << 46;
+  d |= static_cast<uint64_t>(2) << 61;
+  return d;
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, shape M = 128 x N.
+template <int N>
+__host__ __device__ constexpr uint32_t idesc_bf16() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
+         (static_cast<uint32_t>(BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// 32 lanes x 32 bits x 16 columns: thread t of the warp gets row (lane base +
+// t), columns col .. col+15.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
+}
+
+__device__ __forceinline__ void epi_bar_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+
+template <int BN, int STAGES>
+struct TcCfg {
+  static constexpr uint32_t A_BYTES = BM * BK * 2;
+  static constexpr uint32_t B_BYTES = BN * BK * 2;
+  static constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
+  static constexpr uint32_t TAIL = (2 * STAGES + 1) * 8 + 6 * BN * 4 + 16;
+  static constexpr uint32_t SMEM = 1024 + STAGES * STAGE_BYTES + TAIL;
+};
+
+template <int BN, int STAGES, bool CPLX>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    step_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int b_row0,
+                   StepArgs a) {
+  using Cfg = TcCfg<BN, STAGES>;
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t* smem = smem_raw + (base - raw);
+  const uint32_t sA = base;
+  const uint32_t sB = base + STAGES * Cfg::A_BYTES;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * Cfg::STAGE_BYTES);
+  float* s_beta = reinterpret_cast<float*>(bars + 2 * STAGES + 1);
+  float* s_dsc = s_beta + BN;
+  float* s_red = s_dsc + BN;  // [4][BN]
+  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(s_red + 4 * BN);
+  int* s_flag = reinterpret_cast<int*>(s_tmem + 1);  // [0] abort, [1] diverged
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int KB = (a.N + BK - 1) / BK;
+  auto full_bar = [&](int s) { return smem_u32(bars + s); };
+  auto empty_bar = [&](int s) { return smem_u32(bars + STAGES + s); };
+  const uint32_t acc_bar = smem_u32(bars + 2 * STAGES);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(empty_bar(s), 1);
+    }
+    mbar_init(acc_bar, 1);
+    s_flag[0] = 0;
+    s_flag[1] = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) tmem_alloc(smem_u32(s_tmem), BN);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *s_tmem;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int issued = 0;
+      for (int kb = 0; kb < KB; ++kb) {
+        const int s = kb % STAGES;
+        const uint32_t ph = (kb / STAGES) & 1;
+        if (!mbar_wait(empty_bar(s), ph ^ 1u) || *(volatile int*)&s_flag[0]) {
+          atomicOr(&s_flag[0], 1);
+          break;
+        }
+        mbar_arrive_expect_tx(full_bar(s), Cfg::STAGE_BYTES);
+        tma_load_2d(sA + s * Cfg::A_BYTES, &tmA, kb * BK, m0, full_bar(s));
+        tma_load_2d(sB + s * Cfg::B_BYTES, &tmB, kb * BK, b_row0 + n0, full_bar(s));
+        ++issued;
+      }
+      if (*(volatile int*)&s_flag[0]) {
+        // drain the loads still in flight before the CTA can exit
+        for (int kb = issued - 1; kb >= 0 && kb >= issued - STAGES; --kb)
+          (void)mbar_wait(full_bar(kb % STAGES), (kb / STAGES) & 1);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_bf16<BN>();
+      for (int kb = 0; kb < KB; ++kb) {
+        const int s = kb % STAGES;
+        const uint32_t ph = (kb / STAGES) & 1;
+        if (!mbar_wait(full_bar(s), ph) || *(volatile int*)&s_flag[0]) {
+          atomicOr(&s_flag[0], 1);
+          break;
+        }
+        tc_fence_after();
+#pragma unroll
+        for (int k = 0; k < BK / 16; ++k) {
+          mma_bf16(tmem, sdesc_sw128(sA + s * Cfg::A_BYTES + k * 32), sdesc_sw128(sB + s * Cfg::B_BYTES + k * 32),
+                   idesc, (kb | k) != 0);
+        }
+        mma_commit(empty_bar(s));
+      }
+      mma_commit(acc_bar);  // tracks every MMA issued above, also after an abort
+    }
+  } else {
+    // ---------------- epilogue warps ----------------
+    constexpr int RPT = CPLX ? BN / 2 : BN;
+    const int e = threadIdx.x - 64;
+    const int rbase = CPLX ? n0 / 2 : n0;
+    if (e < RPT) {
+      const int r = rbase + e;
+      const float b = r < a.R ? a.beta_in[r] : 1.0f;
+      s_beta[e] = stage_beta(a, b);
+      s_dsc[e] = r < a.R ? noise_scale(a, r) : 0.0f;
+    }
+    epi_bar_sync();
+    const bool ok = __all_sync(0xffffffffu, mbar_wait(acc_bar, 0));
+    tc_fence_after();
+    const int q = warp & 3;
+    const int half = (warp - 2) >> 2;
+    const int i = m0 + 32 * q + lane;
+    const uint32_t taddr = tmem + (static_cast<uint32_t>(32 * q) << 16);
+    constexpr int U = CPLX ? 2 : 4;
+    constexpr int CH = BN / 32;  // 16-column chunks per half
+    int bad = 0;
+    if (ok && !*(volatile int*)&s_flag[0]) {
+      for (int ch = half * CH; ch < (half + 1) * CH; ++ch) {
+        float v[16];
+        tmem_ld16(taddr + ch * 16, v);
+        float red[16];
+#pragma unroll
+        for (int gq = 0; gq < 4; ++gq) {
+          const int c0 = n0 + ch * 16 + 4 * gq;
+          const int lr0 = CPLX ? (ch * 16 + 4 * gq) / 2 : ch * 16 + 4 * gq;
+          if (i < a.N) {
+            epi_quad<CPLX>(a, i, c0, &v[4 * gq], &s_beta[lr0], &s_dsc[lr0], &red[U * gq], bad);
+          } else {
+#pragma unroll
+            for (int u = 0; u < U; ++u) red[U * gq + u] = 0.0f;
+          }
+        }
+        // reduce over the 32 rows of this warp, one value per local restart
+#pragma unroll
+        for (int u = 0; u < 4 * U; ++u) {
+          float x = red[u];
+#pragma unroll
+          for (int off = 16; off; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+          if (lane == 0) s_red[q * BN + (CPLX ? ch * 8 : ch * 16) + u] = x;
+        }
+      }
+    } else {
+      if (lane == 0) atomicOr(a.err, E_TIMEOUT);
+    }
+    if (bad) s_flag[1] = 1;
+    epi_bar_sync();
+    float* out = (a.mode == M_ENERGY) ? a.e_part : (step_completes(a.mode) ? a.rho_out : nullptr);
+    if (ok && e < RPT) {
+      const int r = rbase + e;
+      if (r < a.R) {
+        if (out)
+          out[size_t(blockIdx.y) * a.Rp + r] = s_red[e] + s_red[BN + e] + s_red[2 * BN + e] + s_red[3 * BN + e];
+        if (blockIdx.y == 0 && step_completes(a.mode)) a.beta_out[r] = next_beta(a, a.beta_in[r]);
+      }
+    }
+    if (e == 0 && s_flag[1]) atomicOr(a.err, E_DIVERGED);
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x == 0 && s_flag[0]) atomicOr(a.err, E_TIMEOUT);
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, BN);
+  }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn get_encode() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+// 2-D BF16 tensor [rows][Np] with a {64, box_rows} box and 128-byte swizzle.
+bool make_map(CUtensorMap* m, const void* ptr, int Np, int rows, int box_rows) {
+  EncodeTiledFn enc = get_encode();
+  if (!enc) return false;
+  const cuuint64_t dims[2] = {static_cast<cuuint64_t>(Np), static_cast<cuuint64_t>(rows)};
+  const cuuint64_t strides[1] = {static_cast<cuuint64_t>(Np) * 2};
+  const cuuint32_t box[2] = {static_cast<cuuint32_t>(BK), static_cast<cuuint32_t>(box_rows)};
+  const cuuint32_t es[2] = {1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int BN, int STAGES, bool CPLX>
+cudaError_t launch_cfg(const CUtensorMap& A, const CUtensorMap& B, int b_row0, const StepArgs& a, cudaStream_t s) {
+  using Cfg = TcCfg<BN, STAGES>;
+  static bool attr_set = false;
+  auto kern = step_tc_kernel<BN, STAGES, CPLX>;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  dim3 grid((a.C + BN - 1) / BN, (a.N + BM - 1) / BM);
+  kern<<<grid, NTHREADS, Cfg::SMEM, s>>>(A, B, b_row0, a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+struct TcPlan {
+  CUtensorMap A;
+  CUtensorMap B128;
+  int Cp;
+};
+
+int tc_mtiles(int N) { return (N + BM - 1) / BM; }
+
+bool tc_supported(int device) {
+  int major = 0, minor = 0;
+  if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, device) != cudaSuccess) return false;
+  if (cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, device) != cudaSuccess) return false;
+  return major == 10 && minor == 3 && get_encode() != nullptr;
+}
+
+cudaError_t tc_plan_create(TcPlan** plan, const __nv_bfloat16* J16, int Np, const __nv_bfloat16* ops, int n_op_bufs,
+                           int Cp) {
+  TcPlan* p = new TcPlan();
+  p->Cp = Cp;
+  if (!make_map(&p->A, J16, Np, Np, BM) || !make_map(&p->B128, ops, Np, n_op_bufs * Cp, 128)) {
+    delete p;
+    return cudaErrorInvalidValue;
+  }
+  *plan = p;
+  return cudaSuccess;
+}
+
+void tc_plan_destroy(TcPlan* plan) { delete plan; }
+
+cudaError_t launch_step_tc(const TcPlan* plan, const StepArgs& a, int op_buf, cudaStream_t s) {
+  const int b_row0 = op_buf * plan->Cp;
+  if (a.cplx) return launch_cfg<128, 4, true>(plan->A, plan->B128, b_row0, a, s);
+  return launch_cfg<128, 4, false>(plan->A, plan->B128, b_row0, a, s);
+}
+
+}  // namespace gda

@@ -1,0 +1,235 @@
+"""Thin Python binding of the C ABI in include/gda.h (argument marshalling only).
+
+Every computation runs in libgda.so's CUDA kernels.  Loading fails loudly if
+the library has not been built (`python -m paper_1807_00699_gb300._build` or
+`__graft_entry__.build()`); there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgda.so")
+
+ISING, XY = 0, 1
+EULER, RK4 = 0, 1
+FP32, BF16 = 0, 1
+
+STATUS = {0: "GDA_OK", 1: "GDA_ERR_INVALID", 2: "GDA_ERR_CUDA", 3: "GDA_ERR_OOM", 4: "GDA_ERR_DIVERGED",
+          5: "GDA_ERR_TIMEOUT", 6: "GDA_ERR_UNSUPPORTED", 7: "GDA_ERR_STATE"}
+
+# Every symbol include/gda.h declares, with its ctypes signature.
+_D = ct.POINTER(ct.c_double)
+_F = ct.POINTER(ct.c_float)
+_VP = ct.c_void_p
+
+
+class Params(ct.Structure):
+    """gda_params (include/gda.h)."""
+    _fields_ = [("integ", ct.c_int32), ("prec", ct.c_int32), ("dt", ct.c_double), ("eps", ct.c_double),
+                ("rho_th", ct.c_double), ("gamma0", ct.c_double), ("beta0", ct.c_double),
+                ("eps_hat", ct.c_double), ("noise_D", ct.c_double), ("noise_decay", ct.c_int32),
+                ("energy_every", ct.c_int32), ("seed", ct.c_uint64), ("init_mode", ct.c_int32),
+                ("reserved0", ct.c_int32), ("init_amp", ct.c_double)]
+
+
+SIGNATURES = {
+    "gda_default_params": (None, [ct.POINTER(Params)]),
+    "gda_create": (ct.c_int, [_D, _D, ct.c_int32, ct.c_int32, ct.POINTER(_VP)]),
+    "gda_load": (ct.c_int, [_VP, _D, _D]),
+    "gda_load_dev": (ct.c_int, [_VP, _VP, _VP]),
+    "gda_set_stream": (ct.c_int, [_VP, _VP]),
+    "gda_run": (ct.c_int, [_VP, ct.POINTER(Params), ct.c_int32, ct.c_int64]),
+    "gda_sync": (ct.c_int, [_VP]),
+    "gda_energy": (ct.c_int, [_VP, _D]),
+    "gda_energy_dev": (ct.c_int, [_VP, _VP]),
+    "gda_best": (ct.c_int, [_VP, _D, ct.POINTER(ct.c_int32), _VP]),
+    "gda_get_state": (ct.c_int, [_VP, _F, _F, _F, ct.POINTER(ct.c_int64)]),
+    "gda_set_state": (ct.c_int, [_VP, _F, _F, _F, ct.c_int32, ct.c_int64]),
+    "gda_trace": (ct.c_int, [_VP, ct.POINTER(ct.c_int64), _D, ct.POINTER(ct.c_int32), ct.c_int32,
+                             ct.POINTER(ct.c_int32)]),
+    "gda_coupling": (ct.c_int, [_VP, ct.c_int32, ct.c_int32, _F, _F]),
+    "gda_kernel_launches": (ct.c_int64, [_VP]),
+    "gda_last_error": (ct.c_char_p, [_VP]),
+    "gda_status_string": (ct.c_char_p, [ct.c_int]),
+    "gda_destroy": (None, [_VP]),
+}
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ct.CDLL:
+    """Loads libgda.so and binds every declared symbol (raises if absent)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build() "
+                           "(the CUDA library is required; there is no CPU fallback)")
+    lib = ct.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class GdaError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _ptr(a: np.ndarray, typ):
+    return a.ctypes.data_as(ct.POINTER(typ))
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    load_library().gda_default_params(ct.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise AttributeError(k)
+        setattr(p, k, v)
+    return p
+
+
+class Solver:
+    """One gda_ctx: an N-spin instance on the current CUDA device."""
+
+    def __init__(self, J: np.ndarray, g: np.ndarray | None = None, model: int = ISING, stream=None):
+        lib = load_library()
+        self._lib = lib
+        J = np.ascontiguousarray(J, dtype=np.float64)
+        if J.ndim != 2 or J.shape[0] != J.shape[1]:
+            raise ValueError("J must be square")
+        self.N = J.shape[0]
+        self.model = model
+        gp = None
+        if g is not None:
+            g = np.ascontiguousarray(g, dtype=np.float64)
+            gp = _ptr(g, ct.c_double)
+        h = _VP()
+        st = lib.gda_create(_ptr(J, ct.c_double), gp, self.N, model, ct.byref(h))
+        if st != 0:
+            raise GdaError(st, "gda_create failed")
+        self._h = h
+        self.R = 0
+        if stream is not None:
+            self.set_stream(stream)
+
+    # -- helpers
+    def _check(self, st: int):
+        if st != 0:
+            raise GdaError(st, self._lib.gda_last_error(self._h).decode())
+
+    @property
+    def width(self) -> int:
+        return 2 if self.model == XY else 1
+
+    def set_stream(self, stream):
+        """stream: a torch.cuda.Stream, a raw cudaStream_t integer, or None."""
+        handle = getattr(stream, "cuda_stream", stream)
+        self._check(self._lib.gda_set_stream(self._h, _VP(handle or 0)))
+
+    def load(self, J: np.ndarray, g: np.ndarray | None = None):
+        J = np.ascontiguousarray(J, dtype=np.float64)
+        gp = None if g is None else _ptr(np.ascontiguousarray(g, dtype=np.float64), ct.c_double)
+        self._check(self._lib.gda_load(self._h, _ptr(J, ct.c_double), gp))
+
+    def load_dev(self, J_ptr: int, g_ptr: int | None = None):
+        self._check(self._lib.gda_load_dev(self._h, _VP(J_ptr), _VP(g_ptr or 0)))
+
+    def run(self, params: Params, R: int, steps: int):
+        self._check(self._lib.gda_run(self._h, ct.byref(params), int(R), int(steps)))
+        self.R = int(R)
+
+    def sync(self):
+        self._check(self._lib.gda_sync(self._h))
+
+    def energy(self) -> np.ndarray:
+        E = np.empty(self.R, dtype=np.float64)
+        self._check(self._lib.gda_energy(self._h, _ptr(E, ct.c_double)))
+        return E
+
+    def energy_dev(self, E_ptr: int):
+        self._check(self._lib.gda_energy_dev(self._h, _VP(E_ptr)))
+
+    def best(self, with_cfg: bool = True):
+        """(E, r, cfg): cfg int8 spins (Ising) or float64 theta (XY)."""
+        E = ct.c_double()
+        r = ct.c_int32()
+        cfg = None
+        cp = None
+        if with_cfg:
+            cfg = np.empty(self.N, dtype=np.float64 if self.model == XY else np.int8)
+            cp = cfg.ctypes.data_as(_VP)
+        self._check(self._lib.gda_best(self._h, ct.byref(E), ct.byref(r), cp))
+        return E.value, r.value, cfg
+
+    def get_state(self):
+        R, N, W = self.R, self.N, self.width
+        psi = np.empty(R * N * W, dtype=np.float32)
+        gam = np.empty(R * N, dtype=np.float32)
+        beta = np.empty(R, dtype=np.float32)
+        step = ct.c_int64()
+        self._check(self._lib.gda_get_state(self._h, _ptr(psi, ct.c_float), _ptr(gam, ct.c_float),
+                                            _ptr(beta, ct.c_float), ct.byref(step)))
+        psi = psi.reshape(R, N, W)
+        psi = psi[..., 0] + 1j * psi[..., 1] if W == 2 else psi[..., 0]
+        return psi, gam.reshape(R, N), beta, step.value
+
+    def set_state(self, psi: np.ndarray, gamma: np.ndarray | None = None, beta: np.ndarray | None = None,
+                  step: int = 0):
+        psi = np.asarray(psi)
+        R = psi.shape[0]
+        if self.model == XY:
+            flat = np.stack([psi.real, psi.imag], axis=-1).astype(np.float32).ravel()
+        else:
+            flat = np.ascontiguousarray(psi, dtype=np.float32).ravel()
+        gp = None if gamma is None else _ptr(np.ascontiguousarray(gamma, dtype=np.float32), ct.c_float)
+        bp = None if beta is None else _ptr(np.ascontiguousarray(beta, dtype=np.float32), ct.c_float)
+        self._check(self._lib.gda_set_state(self._h, _ptr(flat, ct.c_float), gp, bp, R, int(step)))
+        self.R = R
+
+    def trace(self, cap: int = 65536):
+        steps = np.empty(cap, dtype=np.int64)
+        E = np.empty(cap, dtype=np.float64)
+        r = np.empty(cap, dtype=np.int32)
+        n = ct.c_int32()
+        self._check(self._lib.gda_trace(self._h, _ptr(steps, ct.c_int64), _ptr(E, ct.c_double),
+                                        _ptr(r, ct.c_int32), cap, ct.byref(n)))
+        m = min(n.value, cap)
+        return steps[:m], E[:m], r[:m]
+
+    def coupling(self, X: np.ndarray, prec: int = FP32) -> np.ndarray:
+        """Y = J0 X (the coupling product alone) for X of shape (R, N)."""
+        X = np.asarray(X)
+        R = X.shape[0]
+        if self.model == XY:
+            flat = np.stack([X.real, X.imag], axis=-1).astype(np.float32).ravel()
+        else:
+            flat = np.ascontiguousarray(X, dtype=np.float32).ravel()
+        Y = np.empty_like(flat)
+        self._check(self._lib.gda_coupling(self._h, prec, R, _ptr(flat, ct.c_float), _ptr(Y, ct.c_float)))
+        self.R = R
+        Y = Y.reshape(R, self.N, self.width)
+        return Y[..., 0] + 1j * Y[..., 1] if self.model == XY else Y[..., 0]
+
+    def kernel_launches(self) -> int:
+        return int(self._lib.gda_kernel_launches(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.gda_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
