@@ -165,6 +165,19 @@ gda_status gda_trace(gda_ctx* ctx, int64_t* step, double* E, int32_t* r, int32_t
  * (a following gda_run must start with init_mode 0 or 1).  Synchronises. */
 gda_status gda_coupling(gda_ctx* ctx, int32_t prec, int32_t R, const float* X, float* Y);
 
+/* Tracing: enable (1) or disable (0) per-CTA device timestamps of the
+ * tensor-core step kernel.  When enabled, every step launch overwrites, for
+ * each CTA, eight %globaltimer readings (ns): entry, set-up done, first
+ * operand tile arrived, last MMA issued, accumulator ready, epilogue done,
+ * partial sums written, exit.  Costs one buffer of at most (N/64+1)*4096*64
+ * bytes; timing of a profiled run is not representative of an unprofiled one. */
+gda_status gda_profile(gda_ctx* ctx, int32_t enable);
+
+/* Copies the timestamps of the last profiled step launch to out
+ * (cap_ctas * 8 uint64, CTA-major in launch order y*gridDim.x + x);
+ * *nctas receives the number of CTA records copied.  Synchronises. */
+gda_status gda_profile_read(gda_ctx* ctx, uint64_t* out, int32_t cap_ctas, int32_t* nctas);
+
 /* Number of kernels the library launched on this context since creation. */
 int64_t gda_kernel_launches(const gda_ctx* ctx);
 

@@ -74,6 +74,8 @@ struct gda_ctx {
   long long step = 0;
   bool have_state = false;
   long long launches = 0;
+  unsigned long long* stamps = nullptr;  // per-CTA timestamps of the last step launch
+  int stamp_cap = 0;
   std::string msg;
 };
 
@@ -256,6 +258,8 @@ StepArgs base_args(gda_ctx* c, const gda_params* p, bool tc) {
   a.g = c->g32;
   a.e_part = c->epart;
   a.err = c->err;
+  const long long ctas = (long long)((c->C + 127) / 128) * ((c->N + 127) / 128);
+  a.stamps = (c->stamps && tc && ctas <= c->stamp_cap) ? c->stamps : nullptr;
   return a;
 }
 
@@ -360,6 +364,7 @@ void gda_destroy(gda_ctx* c) {
   dfree(c->d_flags); dfree(c->d_maxabs); dfree(c->d_diag);
   dfree(c->bestE); dfree(c->bestR); dfree(c->cfg8); dfree(c->cfgth);
   dfree(c->t_step); dfree(c->t_E); dfree(c->t_r); dfree(c->t_count); dfree(c->err);
+  dfree(c->stamps);
   delete c;
 }
 
@@ -631,6 +636,34 @@ gda_status gda_trace(gda_ctx* c, int64_t* step, double* E, int32_t* r, int32_t c
   gda_status s = check_err(c);
   if (s != GDA_OK) return s;
   if (count) *count = n;
+  return GDA_OK;
+}
+
+gda_status gda_profile(gda_ctx* c, int32_t enable) {
+  if (!c) return GDA_ERR_INVALID;
+  if (!enable) {
+    CK(cudaStreamSynchronize(c->stream));
+    dfree(c->stamps);
+    c->stamp_cap = 0;
+    return GDA_OK;
+  }
+  if (!c->stamps) {
+    const int ctas = (c->Np / 64) * 4096;  // bound on the CTAs of any step launch
+    CK(dalloc(&c->stamps, size_t(ctas) * 8));
+    CK(cudaMemsetAsync(c->stamps, 0, size_t(ctas) * 8 * sizeof(unsigned long long), c->stream));
+    c->stamp_cap = ctas;
+  }
+  return GDA_OK;
+}
+
+gda_status gda_profile_read(gda_ctx* c, uint64_t* out, int32_t cap_ctas, int32_t* nctas) {
+  if (!c) return GDA_ERR_INVALID;
+  if (!c->stamps) return fail(c, GDA_ERR_STATE, "profiling is not enabled");
+  const int n = std::min(cap_ctas, c->stamp_cap);
+  CK(cudaMemcpyAsync(out, c->stamps, size_t(n) * 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                     c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (nctas) *nctas = n;
   return GDA_OK;
 }
 

@@ -63,7 +63,17 @@ struct StepArgs {
   const float* g;        // field g_i [Np] (energy mode)
   float* e_part;         // [mt_count][Rp] partial energies (energy mode)
   int* err;
+  unsigned long long* stamps;  // per-CTA timestamps [ctas][8], or nullptr
 };
+
+// Nanosecond device clock for the optional per-CTA timestamps.
+__device__ __forceinline__ void stamp(const StepArgs& a, int k) {
+  if (a.stamps) {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    a.stamps[(size_t(blockIdx.y) * gridDim.x + blockIdx.x) * 8 + k] = t;
+  }
+}
 
 // Launchers (return cudaGetLastError() of the launch).
 cudaError_t launch_step_simt(const StepArgs& a, const float* J32, const float* operand, cudaStream_t s);

@@ -14,7 +14,7 @@
 
 #include <cstdio>
 
-#include "epilogue.cuh"
+#include "tc_epilogue.cuh"
 
 namespace gda {
 
@@ -127,6 +127,24 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
   for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
 }
 
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float v[8]) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int k = 0; k < 8; ++k) v[k] = __uint_as_float(r[k]);
+}
+
+template <int CW>
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, float* v) {
+  if (CW == 16)
+    tmem_ld16(taddr, v);
+  else
+    tmem_ld8(taddr, v);
+}
+
 __device__ __forceinline__ void epi_bar_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 
 template <int BN, int STAGES>
@@ -138,7 +156,7 @@ struct TcCfg {
   static constexpr uint32_t SMEM = 1024 + STAGES * STAGE_BYTES + TAIL;
 };
 
-template <int BN, int STAGES, bool CPLX>
+template <int BN, int STAGES, bool CPLX, int MODE>
 __global__ void __launch_bounds__(NTHREADS, 1)
     step_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int b_row0,
                    StepArgs a) {
@@ -164,6 +182,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const uint32_t acc_bar = smem_u32(bars + 2 * STAGES);
 
   if (threadIdx.x == 0) {
+    stamp(a, 0);
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(full_bar(s), 1);
       mbar_init(empty_bar(s), 1);
@@ -178,6 +197,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *s_tmem;
+  if (threadIdx.x == 0) stamp(a, 1);
 
   if (warp == 0) {
     if (lane == 0) {
@@ -211,6 +231,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           break;
         }
         tc_fence_after();
+        if (kb == 0) stamp(a, 2);
 #pragma unroll
         for (int k = 0; k < BK / 16; ++k) {
           mma_bf16(tmem, sdesc_sw128(sA + s * Cfg::A_BYTES + k * 32), sdesc_sw128(sB + s * Cfg::B_BYTES + k * 32),
@@ -218,13 +239,23 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
         mma_commit(empty_bar(s));
       }
+      stamp(a, 3);
       mma_commit(acc_bar);  // tracks every MMA issued above, also after an abort
     }
   } else {
     // ---------------- epilogue warps ----------------
-    constexpr int RPT = CPLX ? BN / 2 : BN;
+    constexpr int W = CPLX ? 2 : 1;
+    constexpr int RPT = BN / W;
+    constexpr int CW = (ModeTraits<MODE>::rk_mid || !CPLX) ? 8 : 16;
+    constexpr int NCH = (BN / 2) / CW;
     const int e = threadIdx.x - 64;
-    const int rbase = CPLX ? n0 / 2 : n0;
+    const int rbase = n0 / W;
+    const int q = warp & 3;
+    const int half = (warp - 2) >> 2;
+    const int i = m0 + 32 * q + lane;
+    const int cbeg = n0 + half * (BN / 2);
+    EpiRegs<MODE, CPLX, CW> R[2];
+    epi_load<MODE, CPLX, CW>(a, i, cbeg, R[0]);  // overlaps the MMAs
     if (e < RPT) {
       const int r = rbase + e;
       const float b = r < a.R ? a.beta_in[r] : 1.0f;
@@ -232,60 +263,59 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       s_dsc[e] = r < a.R ? noise_scale(a, r) : 0.0f;
     }
     epi_bar_sync();
-    const bool ok = __all_sync(0xffffffffu, mbar_wait(acc_bar, 0));
+    const bool ok = __all_sync(0xffffffffu, mbar_wait(acc_bar, 0) && !*(volatile int*)&s_flag[0]);
     tc_fence_after();
-    const int q = warp & 3;
-    const int half = (warp - 2) >> 2;
-    const int i = m0 + 32 * q + lane;
-    const uint32_t taddr = tmem + (static_cast<uint32_t>(32 * q) << 16);
-    constexpr int U = CPLX ? 2 : 4;
-    constexpr int CH = BN / 32;  // 16-column chunks per half
+    if (e == 0) stamp(a, 4);
+    const uint32_t taddr = tmem + (static_cast<uint32_t>(32 * q) << 16) + half * (BN / 2);
+    const bool need_red = MODE == M_ENERGY || ((MODE == M_EULER || MODE == M_RK4) && a.rho_out != nullptr);
     int bad = 0;
-    if (ok && !*(volatile int*)&s_flag[0]) {
-      for (int ch = half * CH; ch < (half + 1) * CH; ++ch) {
-        float v[16];
-        tmem_ld16(taddr + ch * 16, v);
-        float red[16];
+    if (ok) {
+      auto body = [&](int ch, const EpiRegs<MODE, CPLX, CW>& cur, EpiRegs<MODE, CPLX, CW>& nxt) {
+        if (ch + 1 < NCH) epi_load<MODE, CPLX, CW>(a, i, cbeg + (ch + 1) * CW, nxt);
+        float v[CW];
+        tmem_ld<CW>(taddr + ch * CW, v);
+        const int lr0 = (half * (BN / 2) + ch * CW) / W;
+        float red[CW / W];
+        epi_chunk<MODE, CPLX, CW>(a, i, cbeg + ch * CW, v, cur, &s_beta[lr0], &s_dsc[lr0], red, bad);
+        if (need_red) {
 #pragma unroll
-        for (int gq = 0; gq < 4; ++gq) {
-          const int c0 = n0 + ch * 16 + 4 * gq;
-          const int lr0 = CPLX ? (ch * 16 + 4 * gq) / 2 : ch * 16 + 4 * gq;
-          if (i < a.N) {
-            epi_quad<CPLX>(a, i, c0, &v[4 * gq], &s_beta[lr0], &s_dsc[lr0], &red[U * gq], bad);
-          } else {
+          for (int u = 0; u < CW / W; ++u) {
+            float x = red[u];
 #pragma unroll
-            for (int u = 0; u < U; ++u) red[U * gq + u] = 0.0f;
+            for (int off = 16; off; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+            if (lane == 0) s_red[q * BN + lr0 + u] = x;
           }
         }
-        // reduce over the 32 rows of this warp, one value per local restart
-#pragma unroll
-        for (int u = 0; u < 4 * U; ++u) {
-          float x = red[u];
-#pragma unroll
-          for (int off = 16; off; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
-          if (lane == 0) s_red[q * BN + (CPLX ? ch * 8 : ch * 16) + u] = x;
-        }
+      };
+      static_assert(NCH % 2 == 0, "chunks are processed in pairs");
+#pragma unroll 1
+      for (int ch = 0; ch < NCH; ch += 2) {
+        body(ch, R[0], R[1]);
+        body(ch + 1, R[1], R[0]);
       }
     } else {
       if (lane == 0) atomicOr(a.err, E_TIMEOUT);
     }
     if (bad) s_flag[1] = 1;
+    if (e == 0) stamp(a, 5);
     epi_bar_sync();
-    float* out = (a.mode == M_ENERGY) ? a.e_part : (step_completes(a.mode) ? a.rho_out : nullptr);
+    float* out = (MODE == M_ENERGY) ? a.e_part : ((MODE == M_EULER || MODE == M_RK4) ? a.rho_out : nullptr);
     if (ok && e < RPT) {
       const int r = rbase + e;
       if (r < a.R) {
         if (out)
           out[size_t(blockIdx.y) * a.Rp + r] = s_red[e] + s_red[BN + e] + s_red[2 * BN + e] + s_red[3 * BN + e];
-        if (blockIdx.y == 0 && step_completes(a.mode)) a.beta_out[r] = next_beta(a, a.beta_in[r]);
+        if (blockIdx.y == 0 && (MODE == M_EULER || MODE == M_RK4)) a.beta_out[r] = next_beta(a, a.beta_in[r]);
       }
     }
     if (e == 0 && s_flag[1]) atomicOr(a.err, E_DIVERGED);
+    if (e == 0) stamp(a, 6);
   }
 
   tc_fence_before();
   __syncthreads();
   if (threadIdx.x == 0 && s_flag[0]) atomicOr(a.err, E_TIMEOUT);
+  if (threadIdx.x == 0) stamp(a, 7);
   if (warp == 1) {
     tc_fence_after();
     tmem_dealloc(tmem, BN);
@@ -322,11 +352,11 @@ bool make_map(CUtensorMap* m, const void* ptr, int Np, int rows, int box_rows) {
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int BN, int STAGES, bool CPLX>
+template <int BN, int STAGES, bool CPLX, int MODE>
 cudaError_t launch_cfg(const CUtensorMap& A, const CUtensorMap& B, int b_row0, const StepArgs& a, cudaStream_t s) {
   using Cfg = TcCfg<BN, STAGES>;
   static bool attr_set = false;
-  auto kern = step_tc_kernel<BN, STAGES, CPLX>;
+  auto kern = step_tc_kernel<BN, STAGES, CPLX, MODE>;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
     if (e != cudaSuccess) return e;
@@ -335,6 +365,25 @@ cudaError_t launch_cfg(const CUtensorMap& A, const CUtensorMap& B, int b_row0, c
   dim3 grid((a.C + BN - 1) / BN, (a.N + BM - 1) / BM);
   kern<<<grid, NTHREADS, Cfg::SMEM, s>>>(A, B, b_row0, a);
   return cudaGetLastError();
+}
+
+template <int BN, int STAGES, bool CPLX>
+cudaError_t dispatch_cplx(const CUtensorMap& A, const CUtensorMap& B, int b_row0, const StepArgs& a, cudaStream_t s) {
+  switch (a.mode) {
+    case M_EULER: return launch_cfg<BN, STAGES, CPLX, M_EULER>(A, B, b_row0, a, s);
+    case M_RK1: return launch_cfg<BN, STAGES, CPLX, M_RK1>(A, B, b_row0, a, s);
+    case M_RK2: return launch_cfg<BN, STAGES, CPLX, M_RK2>(A, B, b_row0, a, s);
+    case M_RK3: return launch_cfg<BN, STAGES, CPLX, M_RK3>(A, B, b_row0, a, s);
+    case M_RK4: return launch_cfg<BN, STAGES, CPLX, M_RK4>(A, B, b_row0, a, s);
+    case M_ENERGY: return launch_cfg<BN, STAGES, CPLX, M_ENERGY>(A, B, b_row0, a, s);
+    case M_RAW: return launch_cfg<BN, STAGES, CPLX, M_RAW>(A, B, b_row0, a, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <int BN, int STAGES>
+cudaError_t dispatch_mode(const CUtensorMap& A, const CUtensorMap& B, int b_row0, const StepArgs& a, cudaStream_t s) {
+  return a.cplx ? dispatch_cplx<BN, STAGES, true>(A, B, b_row0, a, s) : dispatch_cplx<BN, STAGES, false>(A, B, b_row0, a, s);
 }
 
 }  // namespace
@@ -370,8 +419,7 @@ void tc_plan_destroy(TcPlan* plan) { delete plan; }
 
 cudaError_t launch_step_tc(const TcPlan* plan, const StepArgs& a, int op_buf, cudaStream_t s) {
   const int b_row0 = op_buf * plan->Cp;
-  if (a.cplx) return launch_cfg<128, 4, true>(plan->A, plan->B128, b_row0, a, s);
-  return launch_cfg<128, 4, false>(plan->A, plan->B128, b_row0, a, s);
+  return dispatch_mode<128, 4>(plan->A, plan->B128, b_row0, a, s);
 }
 
 }  // namespace gda

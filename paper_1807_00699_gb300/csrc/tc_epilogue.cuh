@@ -1,0 +1,184 @@
+// Register-staged epilogue of the tensor-core step kernel.
+//
+// Each epilogue thread owns one spin row i and walks its columns in chunks of
+// CW.  All inputs a chunk needs (amplitudes, gains, RK4 accumulators) are
+// loaded into registers one chunk ahead of the arithmetic, and the first chunk
+// is loaded while the MMAs are still running, so global-memory latency is
+// paid about once per kernel instead of once per element.  The arithmetic is
+// the same FP32 expression sequence as epi_quad (epilogue.cuh).
+#pragma once
+#include "epilogue.cuh"
+
+namespace gda {
+
+template <int MODE>
+struct ModeTraits {
+  static constexpr bool rk_mid = MODE == M_RK2 || MODE == M_RK3 || MODE == M_RK4;
+  static constexpr bool has_x = MODE != M_RAW;
+  static constexpr bool has_g = MODE != M_RAW && MODE != M_ENERGY;
+};
+
+template <int MODE, bool CPLX, int CW>
+struct EpiRegs {
+  static constexpr int W = CPLX ? 2 : 1;
+  static constexpr int NR = CW / W;
+  using T = ModeTraits<MODE>;
+  float x[T::has_x ? CW : 1];
+  float pn[T::rk_mid ? CW : 1];
+  float ac[T::rk_mid ? CW : 1];
+  float gs[T::has_g ? NR : 1];
+  float gn[T::rk_mid ? NR : 1];
+  float ga[T::rk_mid ? NR : 1];
+};
+
+// Loads the inputs of columns c0 .. c0+CW-1 at row i.  Every address is
+// inside the padded buffers (rows < Np, columns < Cp), so no branch guards
+// the loads; padded rows and restarts are discarded by epi_chunk.
+template <int MODE, bool CPLX, int CW>
+__device__ __forceinline__ void epi_load(const StepArgs& a, int i, int c0, EpiRegs<MODE, CPLX, CW>& R) {
+  using Tr = ModeTraits<MODE>;
+  constexpr int W = CPLX ? 2 : 1;
+  const size_t Np = a.Np;
+  const int r0 = CPLX ? c0 / 2 : c0;
+#pragma unroll
+  for (int k = 0; k < CW; ++k) {
+    const size_t o = size_t(c0 + k) * Np + i;
+    if (MODE == M_ENERGY) {
+      R.x[k] = a.psi_n[o];
+    } else if (Tr::has_x) {
+      R.x[k] = a.xs[o];
+      if (Tr::rk_mid) {
+        R.pn[k] = a.psi_n[o];
+        R.ac[k] = a.acc[o];
+      }
+    }
+  }
+  if (Tr::has_g) {
+#pragma unroll
+    for (int u = 0; u < CW / W; ++u) {
+      const size_t og = size_t(r0 + u) * Np + i;
+      R.gs[u] = (MODE == M_EULER || MODE == M_RK1) ? a.gam[og] : a.gstg[og];
+      if (Tr::rk_mid) {
+        R.gn[u] = a.gam[og];
+        R.ga[u] = a.gacc[og];
+      }
+    }
+  }
+}
+
+// Arithmetic and stores of one chunk.  y: the CW accumulator values of row i.
+// beta_s / dsc: per-restart stage scale and noise amplitude, indexed by the
+// chunk's local restart.  red[u]: per-restart contribution (density of the
+// new amplitude, or Eq. (1) partial energy).
+template <int MODE, bool CPLX, int CW>
+__device__ __forceinline__ void epi_chunk(const StepArgs& a, int i, int c0, const float* y,
+                                          const EpiRegs<MODE, CPLX, CW>& R, const float* beta_s, const float* dsc,
+                                          float* red, int& bad) {
+  constexpr int W = CPLX ? 2 : 1;
+  constexpr int NR = CW / W;
+  const size_t Np = a.Np;
+  const int r0 = CPLX ? c0 / 2 : c0;
+  const bool row_ok = i < a.N;
+  const float h = row_ok ? a.h1[i] : 0.0f;
+  const float gi = (MODE == M_ENERGY && row_ok) ? a.g[i] : 0.0f;
+  float z[CW];
+  if (MODE == M_EULER || MODE == M_RK4) {
+    bool any = false;
+#pragma unroll
+    for (int u = 0; u < NR; ++u) any |= dsc[u] != 0.0f;
+#pragma unroll
+    for (int q = 0; q < CW / 4; ++q) {
+      if (any) {
+        philox_normal4(uint32_t(i), uint32_t((c0 >> 2) + q), a.step, 0u, a.seed, &z[4 * q]);
+      } else {
+        z[4 * q] = z[4 * q + 1] = z[4 * q + 2] = z[4 * q + 3] = 0.0f;
+      }
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < NR; ++u) {
+    red[u] = 0.0f;
+    const int r = r0 + u;
+    if (!row_ok || r >= a.R) continue;
+    const int k0 = u * W;
+    const size_t o0 = size_t(c0 + k0) * Np + i;
+    const size_t o1 = o0 + Np;
+    const size_t og = size_t(r) * Np + i;
+    const float yr = y[k0], yi = CPLX ? y[k0 + 1] : 0.0f;
+    if (MODE == M_RAW) {
+      a.psi_out[o0] = yr;
+      if (CPLX) a.psi_out[o1] = yi;
+      continue;
+    }
+    if (MODE == M_ENERGY) {
+      const float pr = R.x[k0], pi = CPLX ? R.x[k0 + 1] : 0.0f;
+      float sr, si = 0.0f;
+      if (CPLX) {
+        const float m = sqrtf(pr * pr + pi * pi);
+        sr = m > 0.0f ? pr / m : 1.0f;
+        si = m > 0.0f ? pi / m : 0.0f;
+      } else {
+        sr = pr >= 0.0f ? 1.0f : -1.0f;
+      }
+      red[u] = -(sr * yr + si * yi) + gi * sr;
+      continue;
+    }
+    const float xr = R.x[k0], xi = CPLX ? R.x[k0 + 1] : 0.0f;
+    const float gs = R.gs[u];
+    const float rho = density(xr, xi);
+    const float kr = xr * (gs - rho) + beta_s[u] * yr + h;
+    const float ki = xi * (gs - rho) + beta_s[u] * yi;
+    const float kg = a.eps * (a.rho_th - rho);
+    float nr, ni, ng;
+    if (MODE == M_EULER) {
+      nr = xr + a.dt * kr;
+      ni = xi + a.dt * ki;
+      ng = gs + a.dt * kg;
+    } else {
+      const float pr = (MODE == M_RK1) ? xr : R.pn[ModeTraits<MODE>::rk_mid ? k0 : 0];
+      const float pi = (MODE == M_RK1) ? xi : (CPLX ? R.pn[ModeTraits<MODE>::rk_mid ? k0 + 1 : 0] : 0.0f);
+      const float gn = (MODE == M_RK1) ? gs : R.gn[ModeTraits<MODE>::rk_mid ? u : 0];
+      if (MODE == M_RK4) {
+        nr = pr + a.dt / 6.0f * (R.ac[k0] + kr);
+        ni = CPLX ? pi + a.dt / 6.0f * (R.ac[CPLX ? k0 + 1 : 0] + ki) : 0.0f;
+        ng = gn + a.dt / 6.0f * (R.ga[u] + kg);
+      } else {
+        const float cf = (MODE == M_RK3) ? a.dt : 0.5f * a.dt;
+        if (MODE == M_RK1) {
+          a.acc[o0] = kr;
+          if (CPLX) a.acc[o1] = ki;
+          a.gacc[og] = kg;
+        } else {
+          a.acc[o0] = R.ac[ModeTraits<MODE>::rk_mid ? k0 : 0] + 2.0f * kr;
+          if (CPLX) a.acc[o1] = R.ac[ModeTraits<MODE>::rk_mid ? k0 + 1 : 0] + 2.0f * ki;
+          a.gacc[og] = R.ga[ModeTraits<MODE>::rk_mid ? u : 0] + 2.0f * kg;
+        }
+        const float sr = pr + cf * kr, si = pi + cf * ki;
+        a.xs_next[o0] = sr;
+        if (CPLX) a.xs_next[o1] = si;
+        a.gstg[og] = gn + cf * kg;
+        if (a.op_out) {
+          a.op_out[o0] = __float2bfloat16_rn(sr);
+          if (CPLX) a.op_out[o1] = __float2bfloat16_rn(si);
+        }
+        continue;
+      }
+    }
+    if (MODE == M_EULER || MODE == M_RK4) {
+      nr += dsc[u] * z[k0];
+      if (CPLX) ni += dsc[u] * z[k0 + 1];
+    }
+    a.psi_out[o0] = nr;
+    if (CPLX) a.psi_out[o1] = ni;
+    a.gam[og] = ng;
+    if (a.op_out) {
+      a.op_out[o0] = __float2bfloat16_rn(nr);
+      if (CPLX) a.op_out[o1] = __float2bfloat16_rn(ni);
+    }
+    const float rn = density(nr, ni);
+    red[u] = rn;
+    bad |= !(rn < 1e30f);
+  }
+}
+
+}  // namespace gda

@@ -52,6 +52,8 @@ SIGNATURES = {
     "gda_trace": (ct.c_int, [_VP, ct.POINTER(ct.c_int64), _D, ct.POINTER(ct.c_int32), ct.c_int32,
                              ct.POINTER(ct.c_int32)]),
     "gda_coupling": (ct.c_int, [_VP, ct.c_int32, ct.c_int32, _F, _F]),
+    "gda_profile": (ct.c_int, [_VP, ct.c_int32]),
+    "gda_profile_read": (ct.c_int, [_VP, ct.POINTER(ct.c_uint64), ct.c_int32, ct.POINTER(ct.c_int32)]),
     "gda_kernel_launches": (ct.c_int64, [_VP]),
     "gda_last_error": (ct.c_char_p, [_VP]),
     "gda_status_string": (ct.c_char_p, [ct.c_int]),
@@ -219,6 +221,16 @@ class Solver:
         self.R = R
         Y = Y.reshape(R, self.N, self.width)
         return Y[..., 0] + 1j * Y[..., 1] if self.model == XY else Y[..., 0]
+
+    def profile(self, enable: bool = True):
+        self._check(self._lib.gda_profile(self._h, 1 if enable else 0))
+
+    def profile_read(self, cap_ctas: int = 4096) -> np.ndarray:
+        """(ctas, 8) uint64 nanosecond stamps of the last tensor-core step launch."""
+        buf = np.zeros(cap_ctas * 8, dtype=np.uint64)
+        n = ct.c_int32()
+        self._check(self._lib.gda_profile_read(self._h, _ptr(buf, ct.c_uint64), cap_ctas, ct.byref(n)))
+        return buf[: n.value * 8].reshape(n.value, 8)
 
     def kernel_launches(self) -> int:
         return int(self._lib.gda_kernel_launches(self._h))
