@@ -178,6 +178,36 @@ gda_status gda_profile(gda_ctx* ctx, int32_t enable);
  * *nctas receives the number of CTA records copied.  Synchronises. */
 gda_status gda_profile_read(gda_ctx* ctx, uint64_t* out, int32_t cap_ctas, int32_t* nctas);
 
+/* Allocation-free energy evaluation.  The paper has no counterpart: this
+ * entry point exists for callers that must not allocate device memory while
+ * they run, such as a host that has reserved all GPU memory for its own
+ * pool, or a serving process whose allocator is frozen after start-up; the
+ * context-based calls above allocate on gda_create / gda_run, this one never
+ * calls cudaMalloc, cudaFree or any allocating routine.
+ *
+ * Computes the Eq. (1) energy of the projected spins of R restarts, in FP64,
+ * exactly as gda_energy does, from caller-owned device buffers:
+ *   J_dev   N*N doubles, row-major, symmetric (diagonal counted as in Eq. 1);
+ *   g_dev   N doubles, or NULL for g = 0;
+ *   psi_dev amplitudes in the gda_get_state layout: R*N floats (Ising) or
+ *           R*N interleaved (re, im) float pairs (XY), restart-major;
+ *   E_dev   R doubles, written;
+ *   stream  a cudaStream_t (NULL: legacy default stream).
+ * Its scratch is one file-scope device array of
+ * GDA_NOALLOC_MAX_N/64 * GDA_NOALLOC_MAX_R doubles (2 MiB) that every GPU
+ * loading this library keeps until the process exits.  Sizes beyond
+ * N <= GDA_NOALLOC_MAX_N and R <= GDA_NOALLOC_MAX_R return GDA_ERR_INVALID,
+ * as do NULL buffers, N < 1, R < 1 or an unknown model.
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  All calls
+ * share the array: calls whose work overlaps on the GPU (different streams,
+ * or different threads on one device) race and must be serialised by the
+ * caller.  Asynchronous on `stream`; returns GDA_ERR_CUDA if a launch fails. */
+#define GDA_NOALLOC_MAX_N 4096
+#define GDA_NOALLOC_MAX_R 4096
+gda_status gda_energy_noalloc(const double* J_dev, const double* g_dev, int32_t N, int32_t model,
+                              const float* psi_dev, int32_t R, double* E_dev, void* stream);
+
 /* Number of kernels the library launched on this context since creation. */
 int64_t gda_kernel_launches(const gda_ctx* ctx);
 

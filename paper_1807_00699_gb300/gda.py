@@ -54,6 +54,7 @@ SIGNATURES = {
     "gda_coupling": (ct.c_int, [_VP, ct.c_int32, ct.c_int32, _F, _F]),
     "gda_profile": (ct.c_int, [_VP, ct.c_int32]),
     "gda_profile_read": (ct.c_int, [_VP, ct.POINTER(ct.c_uint64), ct.c_int32, ct.POINTER(ct.c_int32)]),
+    "gda_energy_noalloc": (ct.c_int, [_VP, _VP, ct.c_int32, ct.c_int32, _VP, ct.c_int32, _VP, _VP]),
     "gda_kernel_launches": (ct.c_int64, [_VP]),
     "gda_last_error": (ct.c_char_p, [_VP]),
     "gda_status_string": (ct.c_char_p, [ct.c_int]),
