@@ -83,9 +83,20 @@ typedef struct {
   uint64_t seed;        /* Philox4x32-10 key for noise and initial amplitudes  */
   int32_t init_mode;    /* 0: psi = 0; 1: seeded U(-a, a) per real component;
                            2: continue from the current state (resume)        */
-  int32_t reserved0;
+  int32_t schedule;     /* gda_schedule: how BF16 steps are launched           */
   double init_amp;      /* a for init_mode 1                                   */
 } gda_params;
+
+/* Launch schedule of the tensor-core path.  AUTO picks the resident kernel
+ * for Euler runs whose 128 x 128 tiles all fit on the device at once (every
+ * CTA keeps its tile's FP32 state in tensor memory for a whole segment of
+ * steps, with a grid barrier between steps), else one launch per step (RK4
+ * stage).  Both give the same numbers. */
+typedef enum {
+  GDA_SCHEDULE_AUTO = 0,
+  GDA_SCHEDULE_PER_STEP = 1,
+  GDA_SCHEDULE_RESIDENT = 2 /* GDA_ERR_UNSUPPORTED if not applicable */
+} gda_schedule;
 
 /* Fills p with dt = 0.01, eps = 0.1, rho_th = 1, gamma0 = 0, beta0 = 1,
  * eps_hat = 0, noise off, Euler, FP32, init_mode 1 with a = 1e-3, seed 0. */

@@ -12,20 +12,26 @@
 
 namespace gda {
 
-// Stage coupling scale beta_s of restart r for the launch's mode.  beta
-// obeys d beta/dt = eps_hat (1 - beta) (Eq. 6 with Delta = 1, K = beta J).
+// Every rounding below is explicit (fused multiply-add, IEEE add / multiply /
+// divide / square root), so each kernel that performs an update computes the
+// same bits whatever code surrounds it.
+
+// d beta / dt = eps_hat (1 - beta) (Eq. 6 with Delta = 1, K = beta J).
+__device__ __forceinline__ float beta_rate(float eh, float b) { return __fmul_rn(eh, __fsub_rn(1.0f, b)); }
+
+// Stage coupling scale beta_s of a restart for the launch's mode.
 __device__ __forceinline__ float stage_beta(const StepArgs& a, float b) {
-  const float eh = a.eps_hat, dt = a.dt;
+  const float eh = a.eps_hat, hdt = __fmul_rn(0.5f, a.dt);
   switch (a.mode) {
-    case M_RK2: return b + 0.5f * dt * (eh * (1.0f - b));
+    case M_RK2: return __fmaf_rn(hdt, beta_rate(eh, b), b);
     case M_RK3: {
-      const float b2 = b + 0.5f * dt * (eh * (1.0f - b));
-      return b + 0.5f * dt * (eh * (1.0f - b2));
+      const float b2 = __fmaf_rn(hdt, beta_rate(eh, b), b);
+      return __fmaf_rn(hdt, beta_rate(eh, b2), b);
     }
     case M_RK4: {
-      const float b2 = b + 0.5f * dt * (eh * (1.0f - b));
-      const float b3 = b + 0.5f * dt * (eh * (1.0f - b2));
-      return b + dt * (eh * (1.0f - b3));
+      const float b2 = __fmaf_rn(hdt, beta_rate(eh, b), b);
+      const float b3 = __fmaf_rn(hdt, beta_rate(eh, b2), b);
+      return __fmaf_rn(a.dt, beta_rate(eh, b3), b);
     }
     case M_ENERGY: return 1.0f;
     default: return b;
@@ -34,13 +40,14 @@ __device__ __forceinline__ float stage_beta(const StepArgs& a, float b) {
 
 // beta^{n+1} from beta^n for a completed Euler or RK4 step.
 __device__ __forceinline__ float next_beta(const StepArgs& a, float b) {
-  const float eh = a.eps_hat, dt = a.dt;
-  if (a.mode == M_EULER) return b + dt * (eh * (1.0f - b));
-  const float k1 = eh * (1.0f - b);
-  const float k2 = eh * (1.0f - (b + 0.5f * dt * k1));
-  const float k3 = eh * (1.0f - (b + 0.5f * dt * k2));
-  const float k4 = eh * (1.0f - (b + dt * k3));
-  return b + dt / 6.0f * (k1 + 2.0f * k2 + 2.0f * k3 + k4);
+  const float eh = a.eps_hat, dt = a.dt, hdt = __fmul_rn(0.5f, a.dt);
+  if (a.mode == M_EULER) return __fmaf_rn(dt, beta_rate(eh, b), b);
+  const float k1 = beta_rate(eh, b);
+  const float k2 = beta_rate(eh, __fmaf_rn(hdt, k1, b));
+  const float k3 = beta_rate(eh, __fmaf_rn(hdt, k2, b));
+  const float k4 = beta_rate(eh, __fmaf_rn(dt, k3, b));
+  const float sum = __fadd_rn(__fadd_rn(__fadd_rn(k1, __fmul_rn(2.0f, k2)), __fmul_rn(2.0f, k3)), k4);
+  return __fmaf_rn(__fdiv_rn(dt, 6.0f), sum, b);
 }
 
 __device__ __forceinline__ bool step_completes(int mode) { return mode == M_EULER || mode == M_RK4; }
@@ -53,11 +60,26 @@ __device__ __forceinline__ float noise_scale(const StepArgs& a, int r) {
   float D = a.noise_D;
   if (a.noise_decay) {
     float s = 0.0f;
-    for (int t = 0; t < a.mt_count; ++t) s += a.rho_in[t * a.Rp + r];
-    D *= fmaxf(0.0f, 1.0f - (s / float(a.N)) / a.rho_th);
+    for (int t = 0; t < a.mt_count; ++t) s = __fadd_rn(s, a.rho_in[t * a.Rp + r]);
+    const float ratio = __fdiv_rn(__fdiv_rn(s, float(a.N)), a.rho_th);
+    D = __fmul_rn(D, fmaxf(0.0f, __fsub_rn(1.0f, ratio)));
   }
-  return sqrtf(a.dt) * D * (a.cplx ? 0.70710678118654752f : 1.0f);
+  return __fmul_rn(__fmul_rn(__fsqrt_rn(a.dt), D), a.cplx ? 0.70710678118654752f : 1.0f);
 }
+
+// Right-hand side of Eqs. (2) and (5) for one restart at one spin:
+// k = x (gamma_s - |x|^2) + beta_s y + h,  k_gamma = eps (rho_th - |x|^2).
+__device__ __forceinline__ void gd_rhs(float xr, float xi, float gs, float yr, float yi, float bs, float h, float eps,
+                                       float rho_th, float& kr, float& ki, float& kg) {
+  const float rho = density(xr, xi);
+  const float t = __fsub_rn(gs, rho);
+  kr = __fmaf_rn(xr, t, __fmaf_rn(bs, yr, h));
+  ki = __fmaf_rn(xi, t, __fmul_rn(bs, yi));
+  kg = __fmul_rn(eps, __fsub_rn(rho_th, rho));
+}
+
+// y + a x with one rounding.
+__device__ __forceinline__ float axpy(float a, float x, float y) { return __fmaf_rn(a, x, y); }
 
 // One quad.  beta_s[u], dsc[u]: per-restart stage scale and noise amplitude
 // of the quad's restarts (4 Ising, 2 XY).  red[u] receives |psi^{n+1}|^2
@@ -114,38 +136,37 @@ __device__ __forceinline__ void epi_quad(const StepArgs& a, int i, int c0, const
 
     const float xr = a.xs[o0], xi = CPLX ? a.xs[o1] : 0.0f;
     const float gs = (mode == M_EULER || mode == M_RK1) ? a.gam[og] : a.gstg[og];
-    const float rho = density(xr, xi);
-    const float kr = xr * (gs - rho) + beta_s[u] * yr + h;
-    const float ki = xi * (gs - rho) + beta_s[u] * yi;
-    const float kg = a.eps * (a.rho_th - rho);
+    float kr, ki, kg;
+    gd_rhs(xr, xi, gs, yr, yi, beta_s[u], h, a.eps, a.rho_th, kr, ki, kg);
     float nr, ni, ng;
     if (mode == M_EULER) {
-      nr = xr + a.dt * kr;
-      ni = xi + a.dt * ki;
-      ng = gs + a.dt * kg;
+      nr = axpy(a.dt, kr, xr);
+      ni = axpy(a.dt, ki, xi);
+      ng = axpy(a.dt, kg, gs);
     } else {
       const float pr = (mode == M_RK1) ? xr : a.psi_n[o0];
       const float pi = (mode == M_RK1) ? xi : (CPLX ? a.psi_n[o1] : 0.0f);
       const float gn = (mode == M_RK1) ? gs : a.gam[og];
       if (mode == M_RK4) {
-        nr = pr + a.dt / 6.0f * (a.acc[o0] + kr);
-        ni = CPLX ? pi + a.dt / 6.0f * (a.acc[o1] + ki) : 0.0f;
-        ng = gn + a.dt / 6.0f * (a.gacc[og] + kg);
+        const float d6 = __fdiv_rn(a.dt, 6.0f);
+        nr = axpy(d6, __fadd_rn(a.acc[o0], kr), pr);
+        ni = CPLX ? axpy(d6, __fadd_rn(a.acc[o1], ki), pi) : 0.0f;
+        ng = axpy(d6, __fadd_rn(a.gacc[og], kg), gn);
       } else {
-        const float cf = (mode == M_RK3) ? a.dt : 0.5f * a.dt;
+        const float cf = (mode == M_RK3) ? a.dt : __fmul_rn(0.5f, a.dt);
         if (mode == M_RK1) {
           a.acc[o0] = kr;
           if (CPLX) a.acc[o1] = ki;
           a.gacc[og] = kg;
         } else {
-          a.acc[o0] += 2.0f * kr;
-          if (CPLX) a.acc[o1] += 2.0f * ki;
-          a.gacc[og] += 2.0f * kg;
+          a.acc[o0] = axpy(2.0f, kr, a.acc[o0]);
+          if (CPLX) a.acc[o1] = axpy(2.0f, ki, a.acc[o1]);
+          a.gacc[og] = axpy(2.0f, kg, a.gacc[og]);
         }
-        const float sr = pr + cf * kr, si = pi + cf * ki;
+        const float sr = axpy(cf, kr, pr), si = axpy(cf, ki, pi);
         a.xs_next[o0] = sr;
         if (CPLX) a.xs_next[o1] = si;
-        a.gstg[og] = gn + cf * kg;
+        a.gstg[og] = axpy(cf, kg, gn);
         if (a.op_out) {
           a.op_out[o0] = __float2bfloat16_rn(sr);
           if (CPLX) a.op_out[o1] = __float2bfloat16_rn(si);
@@ -154,8 +175,8 @@ __device__ __forceinline__ void epi_quad(const StepArgs& a, int i, int c0, const
       }
     }
     // completed step: noise, then write psi^{n+1}, gamma^{n+1}
-    nr += dsc[u] * z[(col) & 3];
-    if (CPLX) ni += dsc[u] * z[(col + 1) & 3];
+    nr = axpy(dsc[u], z[(col) & 3], nr);
+    if (CPLX) ni = axpy(dsc[u], z[(col + 1) & 3], ni);
     a.psi_out[o0] = nr;
     if (CPLX) a.psi_out[o1] = ni;
     a.gam[og] = ng;

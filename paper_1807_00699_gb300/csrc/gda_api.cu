@@ -12,6 +12,7 @@
 #include "../../include/gda.h"
 #include "gda_internal.h"
 #include "kernels.h"
+#include "res.h"
 
 using namespace gda;
 
@@ -69,6 +70,7 @@ struct gda_ctx {
   int* t_r = nullptr;
   int* t_count = nullptr;
   int* err = nullptr;
+  unsigned* gbar = nullptr;  // grid-barrier counter of the resident kernel
   TcPlan* plan = nullptr;
   int cur = 0, bcur = 0, rcur = 0, opcur = 0;
   long long step = 0;
@@ -239,6 +241,8 @@ gda_status check_params(gda_ctx* c, const gda_params* p) {
   if (p->noise_D < 0) return fail(c, GDA_ERR_INVALID, "noise_D must be >= 0");
   if (p->init_mode < 0 || p->init_mode > 2) return fail(c, GDA_ERR_INVALID, "init_mode must be 0, 1 or 2");
   if (p->energy_every < 0) return fail(c, GDA_ERR_INVALID, "energy_every must be >= 0");
+  if (p->schedule < GDA_SCHEDULE_AUTO || p->schedule > GDA_SCHEDULE_RESIDENT)
+    return fail(c, GDA_ERR_INVALID, "unknown schedule %d", p->schedule);
   if (p->prec == GDA_BF16 && !c->tc_ok)
     return fail(c, GDA_ERR_UNSUPPORTED, "BF16 tensor-core path needs an sm_103 device");
   return GDA_OK;
@@ -363,7 +367,7 @@ void gda_destroy(gda_ctx* c) {
   dfree(c->J64); dfree(c->J32); dfree(c->J16); dfree(c->Jint); dfree(c->g64); dfree(c->g32); dfree(c->h1);
   dfree(c->d_flags); dfree(c->d_maxabs); dfree(c->d_diag);
   dfree(c->bestE); dfree(c->bestR); dfree(c->cfg8); dfree(c->cfgth);
-  dfree(c->t_step); dfree(c->t_E); dfree(c->t_r); dfree(c->t_count); dfree(c->err);
+  dfree(c->t_step); dfree(c->t_E); dfree(c->t_r); dfree(c->t_count); dfree(c->err); dfree(c->gbar);
   dfree(c->stamps);
   delete c;
 }
@@ -418,6 +422,7 @@ static gda_status create_impl(const double* J, const double* g, int32_t N, int32
   step(dalloc(&c->t_r, kTraceCap));
   step(dalloc(&c->t_count, 1));
   step(dalloc(&c->err, 1));
+  step(dalloc(&c->gbar, 1));
   if (st == GDA_OK) step(cudaMemset(c->err, 0, sizeof(int)));
   if (st == GDA_OK) step(cudaMemset(c->t_count, 0, sizeof(int)));
   if (st == GDA_OK) step(cudaMemset(c->h1, 0, Np * sizeof(float)));
@@ -490,6 +495,47 @@ gda_status gda_run(gda_ctx* c, const gda_params* p, int32_t R, int64_t steps) {
 
   StepArgs base = base_args(c, p, tc);
   const size_t opsz = cn;
+  // Resident persistent kernel: BF16 Euler runs whose tiles all fit on the
+  // device at once run as one launch per tracking segment.
+  const bool resident = tc && p->integ == GDA_EULER && p->schedule != GDA_SCHEDULE_PER_STEP &&
+                        res_fits(c->N, c->C, c->dev);
+  if (p->schedule == GDA_SCHEDULE_RESIDENT && !resident)
+    return fail(c, GDA_ERR_UNSUPPORTED, "resident schedule needs BF16, Euler and a grid that fits the device");
+  if (resident) {
+    const int64_t seg = p->energy_every > 0 ? p->energy_every : steps;
+    for (int64_t k = 0; k < steps; k += seg) {
+      const int64_t len = std::min<int64_t>(seg, steps - k);
+      const int flip = int(len & 1);
+      StepArgs a = base;
+      a.mode = M_EULER;
+      a.step = static_cast<unsigned int>(c->step + k);
+      a.psi_n = c->psi[c->cur];
+      a.beta_in = c->beta[c->bcur];
+      ResArgs ra{};
+      ra.steps = int(len);
+      ra.buf0 = c->opcur;
+      ra.Cp = c->Cp;
+      ra.gbar = c->gbar;
+      ra.psi_final = c->psi[c->cur ^ flip];
+      ra.beta_final = c->beta[c->bcur ^ flip];
+      ra.rho[0] = c->rho[c->rcur];
+      ra.rho[1] = c->rho[c->rcur ^ 1];
+      ra.ops = c->ops;
+      CK(cudaMemsetAsync(c->gbar, 0, sizeof(unsigned), c->stream));
+      LK(launch_step_res(c->plan, ra, a, c->stream));
+      c->cur ^= flip;
+      c->bcur ^= flip;
+      c->opcur ^= flip;
+      if (decay) c->rcur ^= flip;
+      if (p->energy_every > 0 && len == seg) {
+        s = track(c, p, tc, c->step + k + len);
+        if (s != GDA_OK) return s;
+      }
+    }
+    c->step += steps;
+    return GDA_OK;
+  }
+
   for (int64_t k = 0; k < steps; ++k) {
     const long long n = c->step + k;
     StepArgs a = base;

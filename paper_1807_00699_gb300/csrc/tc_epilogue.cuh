@@ -125,38 +125,37 @@ __device__ __forceinline__ void epi_chunk(const StepArgs& a, int i, int c0, cons
     }
     const float xr = R.x[k0], xi = CPLX ? R.x[k0 + 1] : 0.0f;
     const float gs = R.gs[u];
-    const float rho = density(xr, xi);
-    const float kr = xr * (gs - rho) + beta_s[u] * yr + h;
-    const float ki = xi * (gs - rho) + beta_s[u] * yi;
-    const float kg = a.eps * (a.rho_th - rho);
+    float kr, ki, kg;
+    gd_rhs(xr, xi, gs, yr, yi, beta_s[u], h, a.eps, a.rho_th, kr, ki, kg);
     float nr, ni, ng;
     if (MODE == M_EULER) {
-      nr = xr + a.dt * kr;
-      ni = xi + a.dt * ki;
-      ng = gs + a.dt * kg;
+      nr = axpy(a.dt, kr, xr);
+      ni = axpy(a.dt, ki, xi);
+      ng = axpy(a.dt, kg, gs);
     } else {
       const float pr = (MODE == M_RK1) ? xr : R.pn[ModeTraits<MODE>::rk_mid ? k0 : 0];
       const float pi = (MODE == M_RK1) ? xi : (CPLX ? R.pn[ModeTraits<MODE>::rk_mid ? k0 + 1 : 0] : 0.0f);
       const float gn = (MODE == M_RK1) ? gs : R.gn[ModeTraits<MODE>::rk_mid ? u : 0];
       if (MODE == M_RK4) {
-        nr = pr + a.dt / 6.0f * (R.ac[k0] + kr);
-        ni = CPLX ? pi + a.dt / 6.0f * (R.ac[CPLX ? k0 + 1 : 0] + ki) : 0.0f;
-        ng = gn + a.dt / 6.0f * (R.ga[u] + kg);
+        const float d6 = __fdiv_rn(a.dt, 6.0f);
+        nr = axpy(d6, __fadd_rn(R.ac[k0], kr), pr);
+        ni = CPLX ? axpy(d6, __fadd_rn(R.ac[CPLX ? k0 + 1 : 0], ki), pi) : 0.0f;
+        ng = axpy(d6, __fadd_rn(R.ga[u], kg), gn);
       } else {
-        const float cf = (MODE == M_RK3) ? a.dt : 0.5f * a.dt;
+        const float cf = (MODE == M_RK3) ? a.dt : __fmul_rn(0.5f, a.dt);
         if (MODE == M_RK1) {
           a.acc[o0] = kr;
           if (CPLX) a.acc[o1] = ki;
           a.gacc[og] = kg;
         } else {
-          a.acc[o0] = R.ac[ModeTraits<MODE>::rk_mid ? k0 : 0] + 2.0f * kr;
-          if (CPLX) a.acc[o1] = R.ac[ModeTraits<MODE>::rk_mid ? k0 + 1 : 0] + 2.0f * ki;
-          a.gacc[og] = R.ga[ModeTraits<MODE>::rk_mid ? u : 0] + 2.0f * kg;
+          a.acc[o0] = axpy(2.0f, kr, R.ac[ModeTraits<MODE>::rk_mid ? k0 : 0]);
+          if (CPLX) a.acc[o1] = axpy(2.0f, ki, R.ac[ModeTraits<MODE>::rk_mid ? k0 + 1 : 0]);
+          a.gacc[og] = axpy(2.0f, kg, R.ga[ModeTraits<MODE>::rk_mid ? u : 0]);
         }
-        const float sr = pr + cf * kr, si = pi + cf * ki;
+        const float sr = axpy(cf, kr, pr), si = axpy(cf, ki, pi);
         a.xs_next[o0] = sr;
         if (CPLX) a.xs_next[o1] = si;
-        a.gstg[og] = gn + cf * kg;
+        a.gstg[og] = axpy(cf, kg, gn);
         if (a.op_out) {
           a.op_out[o0] = __float2bfloat16_rn(sr);
           if (CPLX) a.op_out[o1] = __float2bfloat16_rn(si);
@@ -165,8 +164,8 @@ __device__ __forceinline__ void epi_chunk(const StepArgs& a, int i, int c0, cons
       }
     }
     if (MODE == M_EULER || MODE == M_RK4) {
-      nr += dsc[u] * z[k0];
-      if (CPLX) ni += dsc[u] * z[k0 + 1];
+      nr = axpy(dsc[u], z[k0], nr);
+      if (CPLX) ni = axpy(dsc[u], z[k0 + 1], ni);
     }
     a.psi_out[o0] = nr;
     if (CPLX) a.psi_out[o1] = ni;

@@ -284,3 +284,36 @@ def test_kernel_launches_counted(gda):
     s.sync()
     assert s.kernel_launches() - before >= 10
     s.close()
+
+
+@pytest.mark.parametrize("model,n,R", [("xy", 300, 70), ("ising", 260, 150), ("xy", 1000, 1024)])
+def test_resident_schedule_equals_per_step(gda, model, n, R):
+    # The resident kernel keeps psi and gamma in tensor memory across steps;
+    # its arithmetic and MMA order are those of the per-step kernel, so the
+    # two schedules must agree bit for bit (noise with decay, beta ramp,
+    # tracking segments of 16 steps included).
+    J, g = instance(model, n, 21)
+    kw = dict(dt=0.02, eps=0.2, eps_hat=0.3, beta0=0.4, noise_D=0.03, noise_decay=1, seed=5, init_mode=1,
+              init_amp=0.2, prec=gda.BF16, energy_every=16)
+    out = {}
+    for sched in (gda.PER_STEP, gda.RESIDENT):
+        s = gda.Solver(J, g, gda.XY if model == "xy" else gda.ISING)
+        s.run(gda.default_params(schedule=sched, **kw), R, 40)
+        out[sched] = (s.get_state(), s.trace(), s.energy())
+        s.close()
+    (sa, ta, ea), (sb, tb, eb) = out[gda.PER_STEP], out[gda.RESIDENT]
+    for x, y in zip(sa[:3], sb[:3]):
+        assert np.array_equal(x, y)
+    assert sa[3] == sb[3] == 40
+    for x, y in zip(ta, tb):
+        assert np.array_equal(x, y)
+    assert np.array_equal(ea, eb)
+
+
+def test_resident_schedule_rejects_rk4(gda):
+    J, g = instance("xy", 64, 1)
+    s = gda.Solver(J, g, gda.XY)
+    with pytest.raises(gda.GdaError) as ei:
+        s.run(gda.default_params(prec=gda.BF16, integ=gda.RK4, schedule=gda.RESIDENT), 8, 2)
+    assert ei.value.status == 6
+    s.close()
