@@ -19,6 +19,7 @@ using namespace gda;
 namespace {
 
 constexpr int kTraceCap = 1 << 16;
+constexpr int kMaxResidentTiles = 1024;  // bound on the CTAs of a resident launch
 
 size_t round_up(size_t x, size_t m) { return (x + m - 1) / m * m; }
 
@@ -70,7 +71,7 @@ struct gda_ctx {
   int* t_r = nullptr;
   int* t_count = nullptr;
   int* err = nullptr;
-  unsigned* gbar = nullptr;  // grid-barrier counter of the resident kernel
+  unsigned* flags = nullptr;  // per-tile step flags of the resident kernel
   TcPlan* plan = nullptr;
   int cur = 0, bcur = 0, rcur = 0, opcur = 0;
   long long step = 0;
@@ -367,7 +368,7 @@ void gda_destroy(gda_ctx* c) {
   dfree(c->J64); dfree(c->J32); dfree(c->J16); dfree(c->Jint); dfree(c->g64); dfree(c->g32); dfree(c->h1);
   dfree(c->d_flags); dfree(c->d_maxabs); dfree(c->d_diag);
   dfree(c->bestE); dfree(c->bestR); dfree(c->cfg8); dfree(c->cfgth);
-  dfree(c->t_step); dfree(c->t_E); dfree(c->t_r); dfree(c->t_count); dfree(c->err); dfree(c->gbar);
+  dfree(c->t_step); dfree(c->t_E); dfree(c->t_r); dfree(c->t_count); dfree(c->err); dfree(c->flags);
   dfree(c->stamps);
   delete c;
 }
@@ -422,7 +423,7 @@ static gda_status create_impl(const double* J, const double* g, int32_t N, int32
   step(dalloc(&c->t_r, kTraceCap));
   step(dalloc(&c->t_count, 1));
   step(dalloc(&c->err, 1));
-  step(dalloc(&c->gbar, 1));
+  step(dalloc(&c->flags, kMaxResidentTiles));
   if (st == GDA_OK) step(cudaMemset(c->err, 0, sizeof(int)));
   if (st == GDA_OK) step(cudaMemset(c->t_count, 0, sizeof(int)));
   if (st == GDA_OK) step(cudaMemset(c->h1, 0, Np * sizeof(float)));
@@ -498,7 +499,8 @@ gda_status gda_run(gda_ctx* c, const gda_params* p, int32_t R, int64_t steps) {
   // Resident persistent kernel: BF16 Euler runs whose tiles all fit on the
   // device at once run as one launch per tracking segment.
   const bool resident = tc && p->integ == GDA_EULER && p->schedule != GDA_SCHEDULE_PER_STEP &&
-                        res_fits(c->N, c->C, c->dev);
+                        res_fits(c->N, c->C, c->dev) &&
+                        (long long)((c->C + 127) / 128) * ((c->N + 127) / 128) <= kMaxResidentTiles;
   if (p->schedule == GDA_SCHEDULE_RESIDENT && !resident)
     return fail(c, GDA_ERR_UNSUPPORTED, "resident schedule needs BF16, Euler and a grid that fits the device");
   if (resident) {
@@ -515,13 +517,13 @@ gda_status gda_run(gda_ctx* c, const gda_params* p, int32_t R, int64_t steps) {
       ra.steps = int(len);
       ra.buf0 = c->opcur;
       ra.Cp = c->Cp;
-      ra.gbar = c->gbar;
+      ra.flags = c->flags;
       ra.psi_final = c->psi[c->cur ^ flip];
       ra.beta_final = c->beta[c->bcur ^ flip];
       ra.rho[0] = c->rho[c->rcur];
       ra.rho[1] = c->rho[c->rcur ^ 1];
       ra.ops = c->ops;
-      CK(cudaMemsetAsync(c->gbar, 0, sizeof(unsigned), c->stream));
+      CK(cudaMemsetAsync(c->flags, 0, kMaxResidentTiles * sizeof(unsigned), c->stream));
       LK(launch_step_res(c->plan, ra, a, c->stream));
       c->cur ^= flip;
       c->bcur ^= flip;

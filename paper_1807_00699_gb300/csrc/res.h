@@ -10,7 +10,7 @@ struct ResArgs {
   int steps;                // steps run by this launch
   int buf0;                 // operand buffer holding bf16(psi) of the first step
   int Cp;                   // rows of one operand buffer
-  unsigned* gbar;           // grid-barrier arrival counter, zero at launch
+  unsigned* flags;          // per-tile step flags [column block][row block], zero at launch
   float* psi_final;         // FP32 amplitudes written after the last step [Cp][Np]
   float* beta_final;        // coupling scale after the last step [Rp]
   float* rho[2];            // density partial sums: rho[0] of the first step's state

@@ -5,12 +5,15 @@
 // in tensor memory: the accumulator (columns 0..127), the amplitudes psi
 // (128..255) and the gains gamma (256..), so per step the only global traffic
 // is the BF16 operand X = bf16(psi) that every CTA reads and writes.  Steps are
-// separated by a grid-wide barrier (an arrival counter with bounded waits):
-// the epilogue of step n writes its slice of X^{n+1}, arrives, and the TMA
-// producer of every CTA waits for all arrivals before loading X^{n+1}.
+// ordered by dataflow flags, one per tile: the epilogue of tile (m, n) writes
+// its slice of X^{n+1} (spins of row block m, columns of block n) and then
+// releases flag[n][m] = step + 1; the producer of every tile in column block n
+// acquires flag[n][kb / 2] before loading K-block kb of X^{n+1}.  Column
+// blocks never wait on each other, and the A (coupling) tiles of the next step
+// are prefetched while the epilogue runs.  Every wait is bounded.
 //
 // Roles: warp 0 TMA producer; warp 1 TMEM allocator + MMA issuer; warps 2..9
-// epilogue (warp w reads TMEM lane quarter w % 4, half of the columns).
+// epilogue (warp w reads TMEM lane quarter w % 4 and a quarter of the columns).
 // Per-element arithmetic is the Euler update of Eqs. (2), (5), (6) with the
 // same FP32 expression sequence as the per-step kernels.
 #include "tc_epilogue.cuh"
@@ -21,7 +24,9 @@ namespace gda {
 namespace {
 
 using namespace ptx;
-constexpr int RES_THREADS = 320;
+constexpr int EPI_WARPS = 16;                 // 4 per tensor-memory lane quarter
+constexpr int RES_THREADS = 64 + 32 * EPI_WARPS;
+constexpr int CPT = 128 / (EPI_WARPS / 4);    // columns per epilogue thread
 constexpr int BN = 128;
 constexpr int STAGES = 6;
 constexpr uint32_t A_BYTES = BM * BK * 2;
@@ -33,13 +38,13 @@ constexpr uint32_t T_GAM = 256;  // tensor-memory column of gamma
 constexpr uint32_t TAIL = (2 * STAGES + 2) * 8 + 8 * BN * 4 + 16;
 constexpr uint32_t SMEM = 1024 + STAGES * STAGE_BYTES + TAIL;
 
-__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"n"(32 * EPI_WARPS) : "memory"); }
 
-// Bounded wait until the grid barrier counter reaches target.
-__device__ __forceinline__ bool grid_wait(const unsigned* gbar, unsigned target) {
-  if (ld_acquire_gpu(gbar) >= target) return true;
+// Bounded wait until a tile flag reaches target (acquire).
+__device__ __forceinline__ bool flag_wait(const unsigned* f, unsigned target) {
+  if (ld_acquire_gpu(f) >= target) return true;
   const long long t0 = clock64();
-  while (ld_acquire_gpu(gbar) < target) {
+  while (ld_acquire_gpu(f) < target) {
     if (clock64() - t0 > kWaitCycles) return false;
   }
   return true;
@@ -51,8 +56,9 @@ __global__ void __launch_bounds__(RES_THREADS, 1)
                     StepArgs a) {
   constexpr int W = CPLX ? 2 : 1;
   constexpr int RPT = BN / W;
-  constexpr int CW = 16;
-  constexpr int NCH = (BN / 2) / CW;
+  constexpr int CW = 8;                 // columns per epilogue chunk
+  constexpr int GR = CW / W;            // restarts per chunk
+  constexpr int NCH = CPT / CW;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
@@ -70,7 +76,6 @@ __global__ void __launch_bounds__(RES_THREADS, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
   const int KB = (a.N + BK - 1) / BK;
-  const unsigned G = gridDim.x * gridDim.y;
   auto full_bar = [&](int s) { return smem_u32(bars + s); };
   auto empty_bar = [&](int s) { return smem_u32(bars + STAGES + s); };
   const uint32_t acc_full = smem_u32(bars + 2 * STAGES);
@@ -99,33 +104,61 @@ __global__ void __launch_bounds__(RES_THREADS, 1)
     // ---------------- TMA producer ----------------
     if (lane == 0) {
       int it = 0;
-      for (int n = 0; n < ra.steps; ++n) {
-        if (n > 0) {
-          if (!grid_wait(ra.gbar, unsigned(n) * G)) {
-            atomicOr(&s_flag[0], 1);
-            break;
-          }
-          fence_proxy_async_global();
-        }
-        if (*(volatile int*)&s_flag[0]) break;
-        const int brow = ((ra.buf0 + n) & 1) * ra.Cp + n0;
-        bool stop = false;
-        for (int kb = 0; kb < KB; ++kb, ++it) {
-          const int s = it % STAGES;
-          const uint32_t ph = (it / STAGES) & 1;
+      const int pre = KB < STAGES ? KB : STAGES;
+      const unsigned* col_flags = ra.flags + size_t(blockIdx.x) * gridDim.y;
+      // ring slots [a_lo, a_hi) have their A tile issued but not yet their B tile
+      int a_lo = 0, a_hi = 0, brow = 0;
+      bool stop = false;
+      for (int n = 0; n < ra.steps && !stop; ++n) {
+        brow = ((ra.buf0 + n) & 1) * ra.Cp + n0;
+        a_lo = a_hi = it;
+        // A tiles of the first `pre` K-blocks do not depend on the previous step
+        for (int kb = 0; kb < pre; ++kb) {
+          const int s = (it + kb) % STAGES;
+          const uint32_t ph = ((it + kb) / STAGES) & 1;
           if (!mbar_wait(empty_bar(s), ph ^ 1u) || *(volatile int*)&s_flag[0]) {
-            atomicOr(&s_flag[0], 1);
             stop = true;
             break;
           }
           mbar_arrive_expect_tx(full_bar(s), STAGE_BYTES);
           tma_load_2d(sA + s * A_BYTES, &tmA, kb * BK, m0, full_bar(s));
-          tma_load_2d(sB + s * B_BYTES, &tmB, kb * BK, brow, full_bar(s));
+          a_hi = it + kb + 1;
         }
         if (stop) break;
+        int ready_m = -1;
+        for (int kb = 0; kb < KB; ++kb, ++it) {
+          const int s = it % STAGES;
+          if (kb >= pre) {
+            const uint32_t ph = (it / STAGES) & 1;
+            if (!mbar_wait(empty_bar(s), ph ^ 1u) || *(volatile int*)&s_flag[0]) {
+              stop = true;
+              break;
+            }
+            mbar_arrive_expect_tx(full_bar(s), STAGE_BYTES);
+            tma_load_2d(sA + s * A_BYTES, &tmA, kb * BK, m0, full_bar(s));
+            a_hi = it + 1;
+          }
+          const int mb = (kb * BK) / BM;  // row block that produced these spins
+          if (n > 0 && mb != ready_m) {
+            if (!flag_wait(col_flags + mb, unsigned(n))) {
+              stop = true;
+              break;
+            }
+            fence_proxy_async_global();
+            ready_m = mb;
+          }
+          tma_load_2d(sB + s * B_BYTES, &tmB, kb * BK, brow, full_bar(s));
+          a_lo = it + 1;
+        }
       }
-      if (*(volatile int*)&s_flag[0]) {
-        for (int k = it - 1; k >= 0 && k >= it - STAGES; --k) (void)mbar_wait(full_bar(k % STAGES), (k / STAGES) & 1);
+      if (stop) {
+        atomicOr(&s_flag[0], 1);
+        // complete every armed slot (the B data is irrelevant now), then wait for
+        // all copies this CTA may still have in flight
+        for (int k = a_lo; k < a_hi; ++k)
+          tma_load_2d(sB + (k % STAGES) * B_BYTES, &tmB, 0, brow, full_bar(k % STAGES));
+        for (int k = a_hi - 1; k >= 0 && k >= a_hi - STAGES; --k)
+          (void)mbar_wait(full_bar(k % STAGES), (k / STAGES) & 1);
       }
     }
   } else if (warp == 1) {
@@ -165,30 +198,30 @@ __global__ void __launch_bounds__(RES_THREADS, 1)
     // ---------------- epilogue ----------------
     const int e = threadIdx.x - 64;
     const int q = warp & 3;
-    const int half = (warp - 2) >> 2;
+    const int part = (warp - 2) >> 2;
     const int i = m0 + 32 * q + lane;
     const bool row_ok = i < a.N;
     const int rbase = n0 / W;
     const size_t Np = a.Np;
     const uint32_t lane_base = static_cast<uint32_t>(32 * q) << 16;
-    const int cb = half * (BN / 2);  // first local column of this thread
+    const int cb = part * CPT;  // first local column of this thread
     const float h = row_ok ? a.h1[i] : 0.0f;
     const bool need_red = a.noise_decay && a.noise_D != 0.0f;
 
     // state -> tensor memory
 #pragma unroll 1
-    for (int ch = 0; ch < NCH; ++ch) {
-      float v[CW];
+    for (int ch = 0; ch < CPT / 16; ++ch) {
+      float v[16];
 #pragma unroll
-      for (int k = 0; k < CW; ++k) v[k] = a.psi_n[size_t(n0 + cb + ch * CW + k) * Np + i];
-      tmem_st16(tmem + lane_base + T_PSI + cb + ch * CW, v);
+      for (int k = 0; k < 16; ++k) v[k] = a.psi_n[size_t(n0 + cb + ch * 16 + k) * Np + i];
+      tmem_st16(tmem + lane_base + T_PSI + cb + ch * 16, v);
     }
 #pragma unroll 1
-    for (int ch = 0; ch < NCH / W; ++ch) {
-      float v[CW];
+    for (int ch = 0; ch < CPT / 16 / W; ++ch) {
+      float v[16];
 #pragma unroll
-      for (int k = 0; k < CW; ++k) v[k] = a.gam[size_t(rbase + cb / W + ch * CW + k) * Np + i];
-      tmem_st16(tmem + lane_base + T_GAM + cb / W + ch * CW, v);
+      for (int k = 0; k < 16; ++k) v[k] = a.gam[size_t(rbase + cb / W + ch * 16 + k) * Np + i];
+      tmem_st16(tmem + lane_base + T_GAM + cb / W + ch * 16, v);
     }
     tmem_st_wait();
     if (e < RPT) {
@@ -199,6 +232,42 @@ __global__ void __launch_bounds__(RES_THREADS, 1)
     StepArgs sa = a;
     sa.mode = M_EULER;
     int bad = 0;
+    const unsigned* col_flags = ra.flags + size_t(blockIdx.x) * gridDim.y;
+
+    const uint32_t tb = tmem + lane_base;
+
+    // one chunk of CW columns: accumulator, amplitudes, gains (8 restarts)
+    struct Chunk {
+      uint32_t y[CW], p[CW], g[GR];
+    };
+    auto issue = [&](int ch, Chunk& t) {
+      const int lc0 = cb + ch * CW;
+      if (CW == 16) {
+        tmem_ld16_nowait(tb + lc0, t.y);
+        tmem_ld16_nowait(tb + T_PSI + lc0, t.p);
+      } else {
+        tmem_ld8_nowait(tb + lc0, t.y);
+        tmem_ld8_nowait(tb + T_PSI + lc0, t.p);
+      }
+      if (GR == 8)
+        tmem_ld8_nowait(tb + T_GAM + lc0 / W, t.g);
+      else
+        tmem_ld4_nowait(tb + T_GAM + lc0 / W, t.g);
+    };
+    auto settle = [&](Chunk& t) {  // wait, then pin every register of t after it
+      if (GR == 8)
+        tmem_wait_ld8(t.g);
+      else
+        tmem_wait_ld4(t.g);
+      if (CW == 16) {
+        tmem_regs_after_wait16(t.y);
+        tmem_regs_after_wait16(t.p);
+      } else {
+        tmem_regs_after_wait8(t.y);
+        tmem_regs_after_wait8(t.p);
+      }
+    };
+
 #pragma unroll 1
     for (int n = 0; n < ra.steps; ++n) {
       sa.step = a.step + unsigned(n);
@@ -206,7 +275,8 @@ __global__ void __launch_bounds__(RES_THREADS, 1)
       if (e < RPT) {
         const int r = rbase + e;
         s_bstage[e] = s_beta[e];
-        if (need_red && n > 0) (void)grid_wait(ra.gbar, unsigned(n) * G);  // partial sums of step n-1
+        if (need_red && n > 0)  // partial sums of step n-1 from every row block of this column block
+          for (unsigned mb = 0; mb < gridDim.y; ++mb) (void)flag_wait(col_flags + mb, unsigned(n));
         s_dsc[e] = r < a.R ? noise_scale(sa, r) : 0.0f;
       }
       epi_sync();
@@ -219,19 +289,11 @@ __global__ void __launch_bounds__(RES_THREADS, 1)
       }
       if (n == 0 && e == 0) stamp(a, 4);
       __nv_bfloat16* op = ra.ops + size_t((ra.buf0 + n + 1) & 1) * ra.Cp * Np;
-#pragma unroll 1
-      for (int ch = 0; ch < NCH; ++ch) {
-        const int lc0 = cb + ch * CW;       // local column of the chunk
-        const int lr0 = lc0 / W;            // local restart
-        uint32_t ry[CW], rp[CW], rg[CW];
-        tmem_ld16_nowait(tmem + lane_base + lc0, ry);
-        tmem_ld16_nowait(tmem + lane_base + T_PSI + lc0, rp);
-        if (CPLX) {
-          tmem_ld8_nowait(tmem + lane_base + T_GAM + lr0, rg);
-        } else {
-          tmem_ld16_nowait(tmem + lane_base + T_GAM + lr0, rg);
-        }
-        tmem_ld_wait();
+
+      auto body = [&](int ch, Chunk& t, Chunk& nxt) {
+        if (ch + 1 < NCH) issue(ch + 1, nxt);  // next chunk's loads overlap this chunk's arithmetic
+        const int lc0 = cb + ch * CW;
+        const int lr0 = lc0 / W;
         const int c0 = n0 + lc0;
         float z[CW];
         bool any = false;
@@ -245,17 +307,15 @@ __global__ void __launch_bounds__(RES_THREADS, 1)
             z[4 * qd] = z[4 * qd + 1] = z[4 * qd + 2] = z[4 * qd + 3] = 0.0f;
           }
         }
-        float npsi[CW], ngam[CW];
-        float red[CW];
+        float npsi[CW], ngam[GR], red[GR];
 #pragma unroll
         for (int u = 0; u < CW / W; ++u) {
           const int k0 = u * W;
-          const float xr = __uint_as_float(rp[k0]), xi = CPLX ? __uint_as_float(rp[k0 + 1]) : 0.0f;
-          const float yr = __uint_as_float(ry[k0]), yi = CPLX ? __uint_as_float(ry[k0 + 1]) : 0.0f;
-          const float gs = __uint_as_float(rg[u]);
-          const float bs = s_bstage[lr0 + u];
+          const float xr = __uint_as_float(t.p[k0]), xi = CPLX ? __uint_as_float(t.p[k0 + 1]) : 0.0f;
+          const float yr = __uint_as_float(t.y[k0]), yi = CPLX ? __uint_as_float(t.y[k0 + 1]) : 0.0f;
+          const float gs = __uint_as_float(t.g[u]);
           float kr, ki, kg;
-          gd_rhs(xr, xi, gs, yr, yi, bs, h, a.eps, a.rho_th, kr, ki, kg);
+          gd_rhs(xr, xi, gs, yr, yi, s_bstage[lr0 + u], h, a.eps, a.rho_th, kr, ki, kg);
           float nr = axpy(a.dt, kr, xr);
           float ni = axpy(a.dt, ki, xi);
           const float ng = axpy(a.dt, kg, gs);
@@ -273,21 +333,33 @@ __global__ void __launch_bounds__(RES_THREADS, 1)
             if (CPLX) op[size_t(c0 + k0 + 1) * Np + i] = __float2bfloat16_rn(ni);
           }
         }
-        tmem_st16(tmem + lane_base + T_PSI + lc0, npsi);
-        if (CPLX) {
-          tmem_st8(tmem + lane_base + T_GAM + lr0, ngam);
-        } else {
-          tmem_st16(tmem + lane_base + T_GAM + lr0, ngam);
-        }
+        if (CW == 16)
+          tmem_st16(tb + T_PSI + lc0, npsi);
+        else
+          tmem_st8(tb + T_PSI + lc0, npsi);
+        if (GR == 8)
+          tmem_st8(tb + T_GAM + lr0, ngam);
+        else
+          tmem_st4(tb + T_GAM + lr0, ngam);
         if (need_red) {
 #pragma unroll
-          for (int u = 0; u < CW / W; ++u) {
+          for (int u = 0; u < GR; ++u) {
             float x = red[u];
 #pragma unroll
             for (int off = 16; off; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
             if (lane == 0) s_red[q * BN + lr0 + u] = x;
           }
         }
+        if (ch + 1 < NCH) settle(nxt);
+      };
+      Chunk c0buf, c1buf;
+      issue(0, c0buf);
+      settle(c0buf);
+      static_assert(NCH % 2 == 0, "chunks are processed in pairs");
+#pragma unroll 1
+      for (int ch = 0; ch < NCH; ch += 2) {
+        body(ch, c0buf, c1buf);
+        body(ch + 1, c1buf, c0buf);
       }
       tmem_st_wait();
       tc_fence_before();
@@ -307,33 +379,31 @@ __global__ void __launch_bounds__(RES_THREADS, 1)
       epi_sync();
       if (e == 0 && n + 1 < ra.steps) {
         __threadfence();
-        red_release_gpu_add(ra.gbar, 1u);
+        st_release_gpu(ra.flags + size_t(blockIdx.x) * gridDim.y + blockIdx.y, unsigned(n + 1));
       }
     }
     // tensor memory -> state
     if (!*(volatile int*)&s_flag[0]) {
 #pragma unroll 1
-      for (int ch = 0; ch < NCH; ++ch) {
-        uint32_t rp[CW];
-        tmem_ld16_nowait(tmem + lane_base + T_PSI + cb + ch * CW, rp);
-        tmem_ld_wait();
+      for (int ch = 0; ch < CPT / 16; ++ch) {
+        float v[16];
+        tmem_ld16(tb + T_PSI + cb + ch * 16, v);
         if (row_ok)
 #pragma unroll
-          for (int k = 0; k < CW; ++k) {
-            const int c = n0 + cb + ch * CW + k;
-            if (c < a.C) ra.psi_final[size_t(c) * Np + i] = __uint_as_float(rp[k]);
+          for (int k = 0; k < 16; ++k) {
+            const int c = n0 + cb + ch * 16 + k;
+            if (c < a.C) ra.psi_final[size_t(c) * Np + i] = v[k];
           }
       }
 #pragma unroll 1
-      for (int ch = 0; ch < NCH / W; ++ch) {
-        uint32_t rg[CW];
-        tmem_ld16_nowait(tmem + lane_base + T_GAM + cb / W + ch * CW, rg);
-        tmem_ld_wait();
+      for (int ch = 0; ch < CPT / 16 / W; ++ch) {
+        float v[16];
+        tmem_ld16(tb + T_GAM + cb / W + ch * 16, v);
         if (row_ok)
 #pragma unroll
-          for (int k = 0; k < CW; ++k) {
-            const int r = rbase + cb / W + ch * CW + k;
-            if (r < a.R) a.gam[size_t(r) * Np + i] = __uint_as_float(rg[k]);
+          for (int k = 0; k < 16; ++k) {
+            const int r = rbase + cb / W + ch * 16 + k;
+            if (r < a.R) a.gam[size_t(r) * Np + i] = v[k];
           }
       }
       if (blockIdx.y == 0 && e < RPT && rbase + e < a.R) ra.beta_final[rbase + e] = s_beta[e];
