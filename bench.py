@@ -209,6 +209,9 @@ def run_ours(args):
     value = units / t_step
     steps_tr, E_tr, _ = s.trace()
     E_ours = Ebest
+    if world > 1:
+        from paper_1807_00699_gb300.replicas import combine_best
+        E_ours = combine_best(Ebest, rbest)[0]  # best answer over the replicas
 
     # dominant kernel alone: the step kernel, no tracking, timed on its stream
     p_k = gda.default_params(dt=W["dt"], eps=W["eps"], rho_th=W["rho_th"], init_mode=1,
