@@ -85,6 +85,7 @@ cudaError_t tc_plan_create(TcPlan** plan, const __nv_bfloat16* J16, int Np,
 void tc_plan_destroy(TcPlan* plan);
 cudaError_t launch_step_tc(const TcPlan* plan, const StepArgs& a, int op_buf, cudaStream_t s);
 int tc_mtiles(int N);
+int tc_pick_bn(int N, int C);
 bool tc_supported(int device);
 
 }  // namespace gda

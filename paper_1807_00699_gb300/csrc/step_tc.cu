@@ -29,10 +29,13 @@ struct TcCfg {
   static constexpr uint32_t A_BYTES = BM * BK * 2;
   static constexpr uint32_t B_BYTES = BN * BK * 2;
   static constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
-  static constexpr uint32_t TAIL = (2 * STAGES + 1) * 8 + 6 * BN * 4 + 16;
+  static constexpr uint32_t TAIL = (2 * STAGES + 4) * 8 + 6 * BN * 4 + 16;
   static constexpr uint32_t SMEM = 1024 + STAGES * STAGE_BYTES + TAIL;
 };
 
+// Persistent over output tiles: CTA b processes tiles b, b + gridDim.x, ...
+// (column block fastest), with two tensor-memory accumulators so that the
+// epilogue of one tile overlaps the MMAs of the next.
 template <int BN, int STAGES, bool CPLX, int MODE>
 __global__ void __launch_bounds__(NTHREADS, 1)
     step_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int b_row0,
@@ -45,18 +48,20 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const uint32_t sA = base;
   const uint32_t sB = base + STAGES * Cfg::A_BYTES;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * Cfg::STAGE_BYTES);
-  float* s_beta = reinterpret_cast<float*>(bars + 2 * STAGES + 1);
+  float* s_beta = reinterpret_cast<float*>(bars + 2 * STAGES + 4);
   float* s_dsc = s_beta + BN;
   float* s_red = s_dsc + BN;  // [4][BN]
   uint32_t* s_tmem = reinterpret_cast<uint32_t*>(s_red + 4 * BN);
   int* s_flag = reinterpret_cast<int*>(s_tmem + 1);  // [0] abort, [1] diverged
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
   const int KB = (a.N + BK - 1) / BK;
+  const int NT = (a.C + BN - 1) / BN;
+  const int T = NT * ((a.N + BM - 1) / BM);
   auto full_bar = [&](int s) { return smem_u32(bars + s); };
   auto empty_bar = [&](int s) { return smem_u32(bars + STAGES + s); };
-  const uint32_t acc_bar = smem_u32(bars + 2 * STAGES);
+  auto acc_full = [&](int b) { return smem_u32(bars + 2 * STAGES + b); };
+  auto acc_empty = [&](int b) { return smem_u32(bars + 2 * STAGES + 2 + b); };
 
   if (threadIdx.x == 0) {
     stamp(a, 0);
@@ -64,12 +69,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       mbar_init(full_bar(s), 1);
       mbar_init(empty_bar(s), 1);
     }
-    mbar_init(acc_bar, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(acc_full(b), 1);
+      mbar_init(acc_empty(b), 1);
+    }
     s_flag[0] = 0;
     s_flag[1] = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 1) tmem_alloc(smem_u32(s_tmem), BN);
+  constexpr uint32_t TCOLS = 2 * BN <= 256 ? 256 : 512;  // power of two
+  if (warp == 1) tmem_alloc(smem_u32(s_tmem), TCOLS);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -77,47 +86,67 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   if (threadIdx.x == 0) stamp(a, 1);
 
   if (warp == 0) {
+    // ---------------- TMA producer ----------------
     if (lane == 0) {
-      int issued = 0;
-      for (int kb = 0; kb < KB; ++kb) {
-        const int s = kb % STAGES;
-        const uint32_t ph = (kb / STAGES) & 1;
-        if (!mbar_wait(empty_bar(s), ph ^ 1u) || *(volatile int*)&s_flag[0]) {
-          atomicOr(&s_flag[0], 1);
-          break;
+      int it = 0;
+      bool stop = false;
+      for (int t = blockIdx.x; t < T && !stop; t += gridDim.x) {
+        const int m0 = (t / NT) * BM, n0 = (t % NT) * BN;
+        for (int kb = 0; kb < KB; ++kb, ++it) {
+          const int s = it % STAGES;
+          const uint32_t ph = (it / STAGES) & 1;
+          if (!mbar_wait(empty_bar(s), ph ^ 1u) || *(volatile int*)&s_flag[0]) {
+            stop = true;
+            break;
+          }
+          mbar_arrive_expect_tx(full_bar(s), Cfg::STAGE_BYTES);
+          tma_load_2d(sA + s * Cfg::A_BYTES, &tmA, kb * BK, m0, full_bar(s));
+          tma_load_2d(sB + s * Cfg::B_BYTES, &tmB, kb * BK, b_row0 + n0, full_bar(s));
         }
-        mbar_arrive_expect_tx(full_bar(s), Cfg::STAGE_BYTES);
-        tma_load_2d(sA + s * Cfg::A_BYTES, &tmA, kb * BK, m0, full_bar(s));
-        tma_load_2d(sB + s * Cfg::B_BYTES, &tmB, kb * BK, b_row0 + n0, full_bar(s));
-        ++issued;
       }
-      if (*(volatile int*)&s_flag[0]) {
-        // drain the loads still in flight before the CTA can exit
-        for (int kb = issued - 1; kb >= 0 && kb >= issued - STAGES; --kb)
-          (void)mbar_wait(full_bar(kb % STAGES), (kb / STAGES) & 1);
+      if (stop) {
+        atomicOr(&s_flag[0], 1);
+        for (int k = it - 1; k >= 0 && k >= it - STAGES; --k) (void)mbar_wait(full_bar(k % STAGES), (k / STAGES) & 1);
       }
     }
   } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
     if (lane == 0) {
       constexpr uint32_t idesc = idesc_bf16<BN>();
-      for (int kb = 0; kb < KB; ++kb) {
-        const int s = kb % STAGES;
-        const uint32_t ph = (kb / STAGES) & 1;
-        if (!mbar_wait(full_bar(s), ph) || *(volatile int*)&s_flag[0]) {
-          atomicOr(&s_flag[0], 1);
+      int it = 0, lt = 0;
+      bool stop = false;
+      for (int t = blockIdx.x; t < T && !stop; t += gridDim.x, ++lt) {
+        const int b = lt & 1;
+        const uint32_t use = lt >> 1;
+        if (!mbar_wait(acc_empty(b), (use & 1) ^ 1u) || *(volatile int*)&s_flag[0]) {
+          stop = true;
           break;
         }
         tc_fence_after();
-        if (kb == 0) stamp(a, 2);
+        const uint32_t dacc = tmem + b * BN;
+        for (int kb = 0; kb < KB; ++kb, ++it) {
+          const int s = it % STAGES;
+          const uint32_t ph = (it / STAGES) & 1;
+          if (!mbar_wait(full_bar(s), ph) || *(volatile int*)&s_flag[0]) {
+            stop = true;
+            break;
+          }
+          tc_fence_after();
+          if (lt == 0 && kb == 0) stamp(a, 2);
 #pragma unroll
-        for (int k = 0; k < BK / 16; ++k) {
-          mma_bf16(tmem, sdesc_sw128(sA + s * Cfg::A_BYTES + k * 32), sdesc_sw128(sB + s * Cfg::B_BYTES + k * 32),
-                   idesc, (kb | k) != 0);
+          for (int k = 0; k < BK / 16; ++k)
+            mma_bf16(dacc, sdesc_sw128(sA + s * Cfg::A_BYTES + k * 32), sdesc_sw128(sB + s * Cfg::B_BYTES + k * 32),
+                     idesc, (kb | k) != 0);
+          mma_commit(empty_bar(s));
         }
-        mma_commit(empty_bar(s));
+        if (lt == 0) stamp(a, 3);
+        mma_commit(acc_full(b));  // also after an abort: tracks every MMA issued into b
+        if (stop) {
+          (void)mbar_wait(acc_full(b), use & 1);  // those MMAs finish before the CTA frees TMEM
+          break;
+        }
       }
-      stamp(a, 3);
-      mma_commit(acc_bar);  // tracks every MMA issued above, also after an abort
+      if (stop) atomicOr(&s_flag[0], 1);
     }
   } else {
     // ---------------- epilogue warps ----------------
@@ -126,27 +155,38 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     constexpr int CW = (ModeTraits<MODE>::rk_mid || !CPLX) ? 8 : 16;
     constexpr int NCH = (BN / 2) / CW;
     const int e = threadIdx.x - 64;
-    const int rbase = n0 / W;
     const int q = warp & 3;
     const int half = (warp - 2) >> 2;
-    const int i = m0 + 32 * q + lane;
-    const int cbeg = n0 + half * (BN / 2);
-    EpiRegs<MODE, CPLX, CW> R[2];
-    epi_load<MODE, CPLX, CW>(a, i, cbeg, R[0]);  // overlaps the MMAs
-    if (e < RPT) {
-      const int r = rbase + e;
-      const float b = r < a.R ? a.beta_in[r] : 1.0f;
-      s_beta[e] = stage_beta(a, b);
-      s_dsc[e] = r < a.R ? noise_scale(a, r) : 0.0f;
-    }
-    epi_bar_sync();
-    const bool ok = __all_sync(0xffffffffu, mbar_wait(acc_bar, 0) && !*(volatile int*)&s_flag[0]);
-    tc_fence_after();
-    if (e == 0) stamp(a, 4);
-    const uint32_t taddr = tmem + (static_cast<uint32_t>(32 * q) << 16) + half * (BN / 2);
     const bool need_red = MODE == M_ENERGY || ((MODE == M_EULER || MODE == M_RK4) && a.rho_out != nullptr);
+    float* out = (MODE == M_ENERGY) ? a.e_part : ((MODE == M_EULER || MODE == M_RK4) ? a.rho_out : nullptr);
     int bad = 0;
-    if (ok) {
+    int lt = 0;
+    EpiRegs<MODE, CPLX, CW> R[2];
+    for (int t = blockIdx.x; t < T; t += gridDim.x, ++lt) {
+      const int mt = t / NT;
+      const int m0 = mt * BM, n0 = (t % NT) * BN;
+      const int b = lt & 1;
+      const uint32_t use = lt >> 1;
+      const int rbase = n0 / W;
+      const int i = m0 + 32 * q + lane;
+      const int cbeg = n0 + half * (BN / 2);
+      epi_load<MODE, CPLX, CW>(a, i, cbeg, R[0]);  // overlaps the MMAs
+      if (e < RPT) {
+        const int r = rbase + e;
+        const float bt = r < a.R ? a.beta_in[r] : 1.0f;
+        s_beta[e] = stage_beta(a, bt);
+        s_dsc[e] = r < a.R ? noise_scale(a, r) : 0.0f;
+      }
+      epi_bar_sync();
+      const bool ok = __all_sync(0xffffffffu, mbar_wait(acc_full(b), use & 1) && !*(volatile int*)&s_flag[0]);
+      tc_fence_after();
+      if (!ok) {
+        if (lane == 0) atomicOr(a.err, E_TIMEOUT);
+        atomicOr(&s_flag[0], 1);
+        break;
+      }
+      if (lt == 0 && e == 0) stamp(a, 4);
+      const uint32_t taddr = tmem + b * BN + (static_cast<uint32_t>(32 * q) << 16) + half * (BN / 2);
       auto body = [&](int ch, const EpiRegs<MODE, CPLX, CW>& cur, EpiRegs<MODE, CPLX, CW>& nxt) {
         if (ch + 1 < NCH) epi_load<MODE, CPLX, CW>(a, i, cbeg + (ch + 1) * CW, nxt);
         float v[CW];
@@ -164,27 +204,27 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           }
         }
       };
-      static_assert(NCH % 2 == 0, "chunks are processed in pairs");
 #pragma unroll 1
-      for (int ch = 0; ch < NCH; ch += 2) {
+      for (int ch = 0; ch + 1 < NCH; ch += 2) {
         body(ch, R[0], R[1]);
         body(ch + 1, R[1], R[0]);
       }
-    } else {
-      if (lane == 0) atomicOr(a.err, E_TIMEOUT);
-    }
-    if (bad) s_flag[1] = 1;
-    if (e == 0) stamp(a, 5);
-    epi_bar_sync();
-    float* out = (MODE == M_ENERGY) ? a.e_part : ((MODE == M_EULER || MODE == M_RK4) ? a.rho_out : nullptr);
-    if (ok && e < RPT) {
-      const int r = rbase + e;
-      if (r < a.R) {
-        if (out)
-          out[size_t(blockIdx.y) * a.Rp + r] = s_red[e] + s_red[BN + e] + s_red[2 * BN + e] + s_red[3 * BN + e];
-        if (blockIdx.y == 0 && (MODE == M_EULER || MODE == M_RK4)) a.beta_out[r] = next_beta(a, a.beta_in[r]);
+      if (NCH & 1) body(NCH - 1, R[0], R[1]);
+      tc_fence_before();
+      epi_bar_sync();
+      if (e == 0) mbar_arrive(acc_empty(b));  // accumulator b may be overwritten
+      if (lt == 0 && e == 0) stamp(a, 5);
+      if (e < RPT) {
+        const int r = rbase + e;
+        if (r < a.R) {
+          if (out)
+            out[size_t(mt) * a.Rp + r] = s_red[e] + s_red[BN + e] + s_red[2 * BN + e] + s_red[3 * BN + e];
+          if (mt == 0 && (MODE == M_EULER || MODE == M_RK4)) a.beta_out[r] = next_beta(a, a.beta_in[r]);
+        }
       }
     }
+    if (bad) s_flag[1] = 1;
+    epi_bar_sync();
     if (e == 0 && s_flag[1]) atomicOr(a.err, E_DIVERGED);
     if (e == 0) stamp(a, 6);
   }
@@ -195,7 +235,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   if (threadIdx.x == 0) stamp(a, 7);
   if (warp == 1) {
     tc_fence_after();
-    tmem_dealloc(tmem, BN);
+    tmem_dealloc(tmem, TCOLS);
   }
 }
 
@@ -239,8 +279,14 @@ cudaError_t launch_cfg(const CUtensorMap& A, const CUtensorMap& B, int b_row0, c
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  dim3 grid((a.C + BN - 1) / BN, (a.N + BM - 1) / BM);
-  kern<<<grid, NTHREADS, Cfg::SMEM, s>>>(A, B, b_row0, a);
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return cudaErrorUnknown;
+  }
+  const int tiles = ((a.C + BN - 1) / BN) * ((a.N + BM - 1) / BM);
+  kern<<<tiles < sms ? tiles : sms, NTHREADS, Cfg::SMEM, s>>>(A, B, b_row0, a);
   return cudaGetLastError();
 }
 
@@ -268,10 +314,37 @@ cudaError_t dispatch_mode(const CUtensorMap& A, const CUtensorMap& B, int b_row0
 struct TcPlan {
   CUtensorMap A;
   CUtensorMap B128;
+  CUtensorMap B224;
+  CUtensorMap B256;
   int Cp;
 };
 
 int tc_mtiles(int N) { return (N + BM - 1) / BM; }
+
+// Tile width for N spins and C columns: the busiest CTA runs ceil(tiles / SMs)
+// tiles, and a 128 x BN tile costs about (128 + BN) shared-memory cycles per
+// K-slice of 16 (MMA reads plus TMA writes of A and B at ~128 B/clk), so pick
+// the width minimising rounds x (128 + BN).
+int tc_pick_bn(int N, int C) {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 148;
+  }
+  const int widths[3] = {128, 224, 256};
+  int best = 128;
+  long long best_cost = -1;
+  for (int bn : widths) {
+    const long long tiles = (long long)((C + bn - 1) / bn) * ((N + BM - 1) / BM);
+    const long long cost = ((tiles + sms - 1) / sms) * (128 + bn);
+    if (best_cost < 0 || cost < best_cost) {
+      best_cost = cost;
+      best = bn;
+    }
+  }
+  return best;
+}
 
 bool tc_supported(int device) {
   int major = 0, minor = 0;
@@ -284,7 +357,8 @@ cudaError_t tc_plan_create(TcPlan** plan, const __nv_bfloat16* J16, int Np, cons
                            int Cp) {
   TcPlan* p = new TcPlan();
   p->Cp = Cp;
-  if (!make_map(&p->A, J16, Np, Np, BM) || !make_map(&p->B128, ops, Np, n_op_bufs * Cp, 128)) {
+  if (!make_map(&p->A, J16, Np, Np, BM) || !make_map(&p->B128, ops, Np, n_op_bufs * Cp, 128) ||
+      !make_map(&p->B224, ops, Np, n_op_bufs * Cp, 224) || !make_map(&p->B256, ops, Np, n_op_bufs * Cp, 256)) {
     delete p;
     return cudaErrorInvalidValue;
   }
@@ -299,7 +373,10 @@ const CUtensorMap* tc_plan_B(const TcPlan* plan) { return &plan->B128; }
 
 cudaError_t launch_step_tc(const TcPlan* plan, const StepArgs& a, int op_buf, cudaStream_t s) {
   const int b_row0 = op_buf * plan->Cp;
-  return dispatch_mode<128, 4>(plan->A, plan->B128, b_row0, a, s);
+  const int bn = tc_pick_bn(a.N, a.C);
+  if (bn == 256) return dispatch_mode<256, 4>(plan->A, plan->B256, b_row0, a, s);
+  if (bn == 224) return dispatch_mode<224, 4>(plan->A, plan->B224, b_row0, a, s);
+  return dispatch_mode<128, 6>(plan->A, plan->B128, b_row0, a, s);
 }
 
 }  // namespace gda

@@ -31,9 +31,10 @@ struct EpiRegs {
   float ga[T::rk_mid ? NR : 1];
 };
 
-// Loads the inputs of columns c0 .. c0+CW-1 at row i.  Every address is
-// inside the padded buffers (rows < Np, columns < Cp), so no branch guards
-// the loads; padded rows and restarts are discarded by epi_chunk.
+// Loads the inputs of columns c0 .. c0+CW-1 at row i.  Column and restart
+// indices are clamped to the padded buffers (columns < Cp, restarts < Rp), so
+// every address is valid whatever the tile width; values of columns beyond C
+// are discarded by epi_chunk.
 template <int MODE, bool CPLX, int CW>
 __device__ __forceinline__ void epi_load(const StepArgs& a, int i, int c0, EpiRegs<MODE, CPLX, CW>& R) {
   using Tr = ModeTraits<MODE>;
@@ -42,7 +43,7 @@ __device__ __forceinline__ void epi_load(const StepArgs& a, int i, int c0, EpiRe
   const int r0 = CPLX ? c0 / 2 : c0;
 #pragma unroll
   for (int k = 0; k < CW; ++k) {
-    const size_t o = size_t(c0 + k) * Np + i;
+    const size_t o = size_t(min(c0 + k, a.Cp - 1)) * Np + i;
     if (MODE == M_ENERGY) {
       R.x[k] = a.psi_n[o];
     } else if (Tr::has_x) {
@@ -56,7 +57,7 @@ __device__ __forceinline__ void epi_load(const StepArgs& a, int i, int c0, EpiRe
   if (Tr::has_g) {
 #pragma unroll
     for (int u = 0; u < CW / W; ++u) {
-      const size_t og = size_t(r0 + u) * Np + i;
+      const size_t og = size_t(min(r0 + u, a.Rp - 1)) * Np + i;
       R.gs[u] = (MODE == M_EULER || MODE == M_RK1) ? a.gam[og] : a.gstg[og];
       if (Tr::rk_mid) {
         R.gn[u] = a.gam[og];

@@ -317,3 +317,33 @@ def test_resident_schedule_rejects_rk4(gda):
         s.run(gda.default_params(prec=gda.BF16, integ=gda.RK4, schedule=gda.RESIDENT), 8, 2)
     assert ei.value.status == 6
     s.close()
+
+
+@pytest.mark.parametrize("model,n,R,seed", [("xy", 1000, 1024, 1), ("ising", 4096, 4096, 3)])
+def test_full_size_sampled_restarts(gda, model, n, R, seed):
+    # The benchmark's XY instance (resident kernel) and the SK N = R = 4096
+    # shape (per-step kernel, wide tiles), BF16 with the coupling ramp, a few
+    # steps; sampled restarts are recomputed by the oracle on their own
+    # (restarts are independent) with BF16-rounded operands.
+    if model == "xy":
+        J, g = synth.xy_gaussian(n, seed)
+        dt = 0.05
+    else:
+        J, g = synth.sk_gaussian(n, seed)
+        dt = 0.1 / math.sqrt(n)
+    kw = dict(dt=dt, eps=0.1, eps_hat=0.05, beta0=0.2, init_amp=0.1, seed=seed)
+    s = gda.Solver(J, g, gda.XY if model == "xy" else gda.ISING)
+    s.run(gda.default_params(init_mode=1, prec=gda.BF16, **kw), R, 3)
+    psi, gam, beta, step = s.get_state()
+    E = s.energy()
+    idx = [0, 1, R // 2 - 1, R // 2, R - 2, R - 1]
+    psi0 = oracle.init_amplitudes(seed, R, n, 0.1, model == "xy")[idx]
+    st = (psi0, np.zeros((len(idx), n)), np.full(len(idx), 0.2))
+    ref, rg, rb = oracle.run(J, g, model, oracle.Params(operand="bf16", **kw), len(idx), 3, state=st)
+    assert amp_err(psi[idx], ref) < 1e-4
+    assert np.allclose(beta[idx], rb, rtol=1e-6)
+    Eref = oracle.energies(J, g, oracle.project(psi[idx].astype(ref.dtype)))
+    assert np.allclose(E[idx], Eref, rtol=1e-9, atol=1e-9)
+    Eb, rb_, _ = s.best(with_cfg=False)
+    assert Eb == E.min() and rb_ == int(np.argmin(E))
+    s.close()
