@@ -275,16 +275,43 @@ def run_ours(args):
         t32 = e0.elapsed_time(e1) / 1e3
         st32, Et32, _ = s32.trace()
         s32.close()
-        Estar = min(E_ours, E32)
+        # BF16 + learned proposal (network settings and start), the proposal's
+        # own cost (features and forward pass) inside the timed region
+        learned = None
+        try:
+            from paper_1807_00699_gb300 import proposal
+            prop = proposal.Proposal()
+        except (OSError, RuntimeError):
+            prop = None
+        if prop is not None:
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            settings = prop.propose(s)
+            e_prop = torch.cuda.Event(enable_timing=True)
+            e_prop.record(stream)
+            s.run(proposal.proposed_params(settings, seed, dt=W["dt"], prec=prec, energy_every=W["energy_every"],
+                                           schedule=sched), W["R"], W["steps"])
+            E_l, _, _ = s.best(with_cfg=False)
+            e1.record(stream)
+            e1.synchronize()
+            st_l, Et_l, _ = s.trace()
+            learned = (E_l, st_l, Et_l, e0.elapsed_time(e1) / 1e3, e0.elapsed_time(e_prop) / 1e3, settings)
+        Estar = min([E_ours, E32] + ([learned[0]] if learned else []))
         target = Estar + 1e-3 * abs(Estar)
 
-        def first_hit(steps_arr, E_arr, t_total):
+        def first_hit(steps_arr, E_arr, t_total, t0=0.0):
             hit = np.nonzero(E_arr <= target)[0]
-            return None if len(hit) == 0 else float(steps_arr[hit[0]]) / W["steps"] * t_total
+            return None if len(hit) == 0 else t0 + float(steps_arr[hit[0]]) / W["steps"] * (t_total - t0)
 
         ttt = {"target_E": target, "E_star_fp64": Estar, "E_best_ours": E_ours, "E_best_fp32": E32,
                "ttt_s_ours": first_hit(steps_tr, E_tr, t_step), "ttt_s_fp32_plain": first_hit(st32, Et32, t32),
                "fp32_solve_s": t32}
+        if learned:
+            ttt.update({"E_best_bf16_learned": learned[0],
+                        "ttt_s_bf16_learned": first_hit(learned[1], learned[2], learned[3], learned[4]),
+                        "learned_settings": learned[5], "proposal_s": learned[4]})
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

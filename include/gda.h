@@ -82,7 +82,8 @@ typedef struct {
   int32_t energy_every; /* k > 0: record the best projected energy every k steps */
   uint64_t seed;        /* Philox4x32-10 key for noise and initial amplitudes  */
   int32_t init_mode;    /* 0: psi = 0; 1: seeded U(-a, a) per real component;
-                           2: continue from the current state (resume)        */
+                           2: continue from the current state (resume);
+                           3: as 1 plus the per-spin base of gda_set_init_base */
   int32_t schedule;     /* gda_schedule: how BF16 steps are launched           */
   double init_amp;      /* a for init_mode 1                                   */
 } gda_params;
@@ -218,6 +219,60 @@ gda_status gda_profile_read(gda_ctx* ctx, uint64_t* out, int32_t cap_ctas, int32
 #define GDA_NOALLOC_MAX_R 4096
 gda_status gda_energy_noalloc(const double* J_dev, const double* g_dev, int32_t N, int32_t model,
                               const float* psi_dev, int32_t R, double* E_dev, void* stream);
+
+/* ---- Learned proposal (not in the paper) --------------------------------
+ * A network that maps an instance's couplings to initial amplitudes and run
+ * settings, trained on configurations the GD algorithm itself finds.  Inputs
+ * are per-spin features (gda_features); the network is a 3-layer MLP
+ * GDA_MLP_IN -> GDA_MLP_HIDDEN -> GDA_MLP_HIDDEN -> GDA_MLP_OUT with ReLU
+ * hidden layers; parameters are one float vector of GDA_MLP_PARAMS entries:
+ * W1 [128][8], b1 [128], W2 [128][128], b2 [128], W3 [5][128], b3 [5].
+ * Outputs per spin: 0, 1 the initial amplitude (real, imaginary part); the
+ * mean over an instance's spins of outputs 2, 3, 4 the instance's settings
+ * (their mapping to epsilon, rho_th and the ramp is the caller's).  All
+ * pointers below are device pointers; calls are asynchronous on `stream`. */
+#define GDA_MLP_IN 8
+#define GDA_MLP_HIDDEN 128
+#define GDA_MLP_OUT 5
+#define GDA_MLP_PARAMS 18309
+
+/* Base amplitude for init_mode 3 (used by the learned proposal): N floats
+ * (Ising) or N interleaved (re, im) float pairs (XY), on the host
+ * (on_device = 0) or the device (1); copied.  A run with init_mode 3 starts
+ * restart r at psi_i = base_i + the init_mode 1 perturbation of (i, r).
+ * Synchronises. */
+gda_status gda_set_init_base(gda_ctx* ctx, const float* base, int32_t on_device);
+
+/* Per-spin features of the context's instance into F_dev [N][8]:
+ * f0 = sum_j J0_ij / |J0_i|, f1 = sum_j |J0_ij| / (sqrt(N) |J0_i|),
+ * f2 = |J0_i|, f3 = max_j |J0_ij| / |J0_i|, f4 = g_i,
+ * f5 = (J0 v1)_i / rms(J0 v1) with v1 = J0 1 / rms(J0 1),
+ * f6 = (J0 f5)_i / rms(J0 f5), f7 = 1 (XY) or 0 (Ising);
+ * J0 = J without its diagonal, |.| Euclidean, rms over spins, 0/0 = 0.
+ * Stream ordered on the context's stream. */
+gda_status gda_features(gda_ctx* ctx, float* F_dev);
+
+/* O [M][5] = MLP(X [M][8]); H (may be NULL) caches the hidden activations
+ * [M][256] for gda_mlp_backward. */
+gda_status gda_mlp_forward(const float* params, const float* X, int32_t M, float* O, float* H, void* stream);
+
+/* G [GDA_MLP_PARAMS] += d(sum_m dO[m] . O[m]) / d params, from the cache of a
+ * forward pass on the same X (G is accumulated with atomics: zero it first). */
+gda_status gda_mlp_backward(const float* params, const float* X, const float* H, const float* dO, int32_t M,
+                            float* G, void* stream);
+
+/* Training loss of n_inst instances (rows [offsets[b], offsets[b+1]) of O):
+ * loss_b = mean_i |a_i - u s_i|^2 + wset * sum_k (mean_i O[i][2+k] - Tset[b][k])^2,
+ * a_i = O[i][0] (+ i O[i][1] if cplx[b]), target spins S [M][2] (re, im),
+ * u the global sign (Ising) or phase (XY) that aligns s with a.  Writes dO
+ * [M][5] = d loss_b / d O and loss [n_inst].  offsets, cplx: device int32. */
+gda_status gda_proposal_loss(const float* O, const float* S, const float* Tset, const int32_t* offsets,
+                             const int32_t* cplx, int32_t n_inst, float wset, float* dO, float* loss,
+                             void* stream);
+
+/* One Adam step (bias corrected, step t >= 1) on P parameters. */
+gda_status gda_adam_step(float* params, const float* grad, float* m1, float* m2, int32_t P, float lr,
+                         float beta1, float beta2, float eps, int32_t t, void* stream);
 
 /* Number of kernels the library launched on this context since creation. */
 int64_t gda_kernel_launches(const gda_ctx* ctx);

@@ -15,15 +15,19 @@ namespace gda {
 
 // ---------------------------------------------------------------- init
 __global__ void k_init_state(float* psi, float* gam, float* beta, int N, int Np, int R, int cplx, int mode,
-                             float amp, float gamma0, float beta0, unsigned long long seed) {
+                             float amp, float gamma0, float beta0, unsigned long long seed, const float* base) {
   const size_t total = size_t(R) * N;
   for (size_t idx = blockIdx.x * size_t(blockDim.x) + threadIdx.x; idx < total; idx += size_t(gridDim.x) * blockDim.x) {
     const int r = int(idx / N), i = int(idx % N);
     float re = 0.0f, im = 0.0f;
-    if (mode == 1) {
+    if (mode == 1 || mode == 3) {
       const U4 o = philox4x32_10(U4{uint32_t(i), uint32_t(r), 0u, 1u}, uint32_t(seed), uint32_t(seed >> 32));
       re = amp * (2.0f * philox_u01(o.x) - 1.0f);
       im = amp * (2.0f * philox_u01(o.y) - 1.0f);
+      if (mode == 3) {  // per-spin base amplitude plus the seeded perturbation
+        re = __fadd_rn(base[2 * i], re);
+        im = __fadd_rn(base[2 * i + 1], im);
+      }
     }
     if (cplx) {
       psi[size_t(2 * r) * Np + i] = re;
@@ -293,9 +297,10 @@ static int grid_for(size_t n) {
 }
 
 cudaError_t launch_init_state(float* psi, float* gam, float* beta, int N, int Np, int R, int cplx, int mode,
-                              float amp, float gamma0, float beta0, unsigned long long seed, cudaStream_t s) {
+                              float amp, float gamma0, float beta0, unsigned long long seed, const float* base,
+                              cudaStream_t s) {
   k_init_state<<<grid_for(size_t(R) * N), 256, 0, s>>>(psi, gam, beta, N, Np, R, cplx, mode, amp, gamma0, beta0,
-                                                        seed);
+                                                        seed, base);
   return cudaGetLastError();
 }
 

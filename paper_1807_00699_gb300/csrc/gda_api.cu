@@ -77,6 +77,8 @@ struct gda_ctx {
   long long step = 0;
   bool have_state = false;
   long long launches = 0;
+  double* fw[2] = {nullptr, nullptr};    // feature scratch [Np]
+  float* base = nullptr;                 // per-spin base amplitude (re, im) for init_mode 3
   unsigned long long* stamps = nullptr;  // per-CTA timestamps of the last step launch
   int stamp_cap = 0;
   std::string msg;
@@ -240,7 +242,8 @@ gda_status check_params(gda_ctx* c, const gda_params* p) {
   if (!(p->dt > 0)) return fail(c, GDA_ERR_INVALID, "dt must be > 0");
   if (!(p->rho_th > 0)) return fail(c, GDA_ERR_INVALID, "rho_th must be > 0");
   if (p->noise_D < 0) return fail(c, GDA_ERR_INVALID, "noise_D must be >= 0");
-  if (p->init_mode < 0 || p->init_mode > 2) return fail(c, GDA_ERR_INVALID, "init_mode must be 0, 1 or 2");
+  if (p->init_mode < 0 || p->init_mode > 3) return fail(c, GDA_ERR_INVALID, "init_mode must be 0, 1, 2 or 3");
+  if (p->init_mode == 3 && !c->base) return fail(c, GDA_ERR_STATE, "init_mode 3 needs gda_set_init_base first");
   if (p->energy_every < 0) return fail(c, GDA_ERR_INVALID, "energy_every must be >= 0");
   if (p->schedule < GDA_SCHEDULE_AUTO || p->schedule > GDA_SCHEDULE_RESIDENT)
     return fail(c, GDA_ERR_INVALID, "unknown schedule %d", p->schedule);
@@ -370,6 +373,9 @@ void gda_destroy(gda_ctx* c) {
   dfree(c->bestE); dfree(c->bestR); dfree(c->cfg8); dfree(c->cfgth);
   dfree(c->t_step); dfree(c->t_E); dfree(c->t_r); dfree(c->t_count); dfree(c->err); dfree(c->flags);
   dfree(c->stamps);
+  dfree(c->fw[0]);
+  dfree(c->fw[1]);
+  dfree(c->base);
   delete c;
 }
 
@@ -477,7 +483,7 @@ gda_status gda_run(gda_ctx* c, const gda_params* p, int32_t R, int64_t steps) {
     s = ensure_state(c, R);
     if (s != GDA_OK) return s;
     LK(launch_init_state(c->psi[0], c->gam, c->beta[0], c->N, c->Np, R, c->cplx, p->init_mode, float(p->init_amp),
-                         float(p->gamma0), float(p->beta0), p->seed, c->stream));
+                         float(p->gamma0), float(p->beta0), p->seed, c->base, c->stream));
     c->cur = 0;
     c->bcur = 0;
     c->step = 0;
@@ -712,6 +718,34 @@ gda_status gda_profile_read(gda_ctx* c, uint64_t* out, int32_t cap_ctas, int32_t
                      c->stream));
   CK(cudaStreamSynchronize(c->stream));
   if (nctas) *nctas = n;
+  return GDA_OK;
+}
+
+gda_status gda_set_init_base(gda_ctx* c, const float* base, int32_t on_device) {
+  if (!c) return GDA_ERR_INVALID;
+  if (!base) return fail(c, GDA_ERR_INVALID, "base is NULL");
+  if (!c->base) {
+    CK(dalloc(&c->base, size_t(2) * c->N));
+  }
+  const size_t W = c->cplx ? 2 : 1;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (W == 2) {
+    CK(cudaMemcpyAsync(c->base, base, size_t(2) * c->N * sizeof(float), kind, c->stream));
+  } else {
+    // real amplitudes: imaginary parts are zero
+    CK(cudaMemsetAsync(c->base, 0, size_t(2) * c->N * sizeof(float), c->stream));
+    CK(cudaMemcpy2DAsync(c->base, 2 * sizeof(float), base, sizeof(float), sizeof(float), c->N, kind, c->stream));
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  return GDA_OK;
+}
+
+gda_status gda_features(gda_ctx* c, float* F) {
+  if (!c) return GDA_ERR_INVALID;
+  if (!F) return fail(c, GDA_ERR_INVALID, "F is NULL");
+  for (int k = 0; k < 2; ++k)
+    if (!c->fw[k]) CK(dalloc(&c->fw[k], size_t(c->Np)));
+  LK(launch_features(c->J64, c->g64, c->N, c->Np, c->cplx, c->fw[0], c->fw[1], F, c->stream));
   return GDA_OK;
 }
 

@@ -9,7 +9,8 @@
 namespace gda {
 
 cudaError_t launch_init_state(float* psi, float* gam, float* beta, int N, int Np, int R, int cplx, int mode,
-                              float amp, float gamma0, float beta0, unsigned long long seed, cudaStream_t s);
+                              float amp, float gamma0, float beta0, unsigned long long seed, const float* base,
+                              cudaStream_t s);
 cudaError_t launch_fill_h1(const double* g, float* h1, int N, float sq, cudaStream_t s);
 cudaError_t launch_to_bf16(const float* x, __nv_bfloat16* y, size_t n, cudaStream_t s);
 cudaError_t launch_rho_partials(bool tc, const float* psi, int N, int Np, int R, int Rp, int cplx, float* out,
@@ -36,4 +37,6 @@ cudaError_t launch_unpack_state(float* psi, float* gam, float* beta, int N, int 
 cudaError_t launch_check_instance(const double* J64, const double* g, int N, int Np, int* flags,
                                   unsigned long long* maxabs, double* diag, cudaStream_t s);
 cudaError_t launch_prepare_J(const double* J64, int Np, float* J32, __nv_bfloat16* J16, int* Jint, cudaStream_t s);
+cudaError_t launch_features(const double* J, const double* g, int N, int Np, int cplx, double* w0, double* w1,
+                            float* F, cudaStream_t s);
 }  // namespace gda

@@ -56,6 +56,13 @@ SIGNATURES = {
     "gda_profile": (ct.c_int, [_VP, ct.c_int32]),
     "gda_profile_read": (ct.c_int, [_VP, ct.POINTER(ct.c_uint64), ct.c_int32, ct.POINTER(ct.c_int32)]),
     "gda_energy_noalloc": (ct.c_int, [_VP, _VP, ct.c_int32, ct.c_int32, _VP, ct.c_int32, _VP, _VP]),
+    "gda_features": (ct.c_int, [_VP, _VP]),
+    "gda_set_init_base": (ct.c_int, [_VP, _VP, ct.c_int32]),
+    "gda_mlp_forward": (ct.c_int, [_VP, _VP, ct.c_int32, _VP, _VP, _VP]),
+    "gda_mlp_backward": (ct.c_int, [_VP, _VP, _VP, _VP, ct.c_int32, _VP, _VP]),
+    "gda_proposal_loss": (ct.c_int, [_VP, _VP, _VP, _VP, _VP, ct.c_int32, ct.c_float, _VP, _VP, _VP]),
+    "gda_adam_step": (ct.c_int, [_VP, _VP, _VP, _VP, ct.c_int32, ct.c_float, ct.c_float, ct.c_float, ct.c_float,
+                                 ct.c_int32, _VP]),
     "gda_kernel_launches": (ct.c_int64, [_VP]),
     "gda_last_error": (ct.c_char_p, [_VP]),
     "gda_status_string": (ct.c_char_p, [ct.c_int]),
@@ -233,6 +240,19 @@ class Solver:
         n = ct.c_int32()
         self._check(self._lib.gda_profile_read(self._h, _ptr(buf, ct.c_uint64), cap_ctas, ct.byref(n)))
         return buf[: n.value * 8].reshape(n.value, 8)
+
+    def set_init_base(self, base: np.ndarray):
+        """Per-spin base amplitude [N] (real or complex) for init_mode 3."""
+        base = np.asarray(base)
+        if self.model == XY:
+            flat = np.stack([base.real, base.imag], axis=-1).astype(np.float32).ravel()
+        else:
+            flat = np.ascontiguousarray(base.real, dtype=np.float32)
+        self._check(self._lib.gda_set_init_base(self._h, flat.ctypes.data_as(_VP), 0))
+
+    def features(self, F_ptr: int):
+        """Per-spin features [N][8] into a device buffer (see gda_features)."""
+        self._check(self._lib.gda_features(self._h, _VP(F_ptr)))
 
     def kernel_launches(self) -> int:
         return int(self._lib.gda_kernel_launches(self._h))

@@ -1,0 +1,296 @@
+"""Learned proposal for the GD solver (not in the paper).
+
+A small network maps an instance's couplings to (a) each spin's initial
+amplitude and (b) the instance's run settings (gain speed eps, threshold
+rho_th, initial coupling scale beta0 of the ramp).  It runs entirely in the
+library's kernels (gda_features, gda_mlp_forward / backward, gda_proposal_loss,
+gda_adam_step); this module only moves buffers and maps the network's outputs
+to parameters.  It is trained on the best configurations and fastest settings
+that plain GD runs find; the plain algorithm stays the fallback and the judge
+(its FP64 energies decide).
+
+Output mapping (o = network output, mean over the instance's spins for 2..4):
+  eps    = 0.02 + 0.48 sigmoid(o2)
+  rho_th = 0.5 + 1.5 sigmoid(o3)
+  beta0  = 0.1 + 0.9 sigmoid(o4)   (ramp d beta/dt = RAMP (1 - beta))
+  psi_i(0) = AMP (o0 + i o1)  plus the library's seeded U(-AMP, AMP) perturbation
+             per restart (init_mode 3, generated on the device).
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import math
+import os
+
+import numpy as np
+
+from . import gda
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+PARAMS_PATH = os.path.join(HERE, "data", "proposal_params.npy")
+NPARAM = 18309
+RAMP = 0.2    # eps_hat of the coupling ramp when beta0 < 1
+AMP = 0.1     # scale of the proposed initial amplitudes
+GRID = [(e, 1.0, b) for e in (0.05, 0.2, 0.5) for b in (0.3, 1.0)]  # (eps, rho_th, beta0) candidates
+
+
+def _sig(x):
+    return 1.0 / (1.0 + math.exp(-x))
+
+
+def _logit(p):
+    return math.log(p / (1.0 - p))
+
+
+def settings_from_outputs(o_mean) -> dict:
+    return {"eps": 0.02 + 0.48 * _sig(o_mean[0]), "rho_th": 0.5 + 1.5 * _sig(o_mean[1]),
+            "beta0": 0.1 + 0.9 * _sig(o_mean[2])}
+
+
+def outputs_from_settings(eps, rho_th, beta0):
+    """Inverse of settings_from_outputs (training targets), clipped inside (0, 1)."""
+    def lg(p):
+        return _logit(min(max(p, 1e-3), 1 - 1e-3))
+    return [lg((eps - 0.02) / 0.48), lg((rho_th - 0.5) / 1.5), lg((beta0 - 0.1) / 0.9)]
+
+
+def run_params(settings: dict, **kw) -> gda.Params:
+    ramp = RAMP if settings["beta0"] < 0.999 else 0.0
+    return gda.default_params(eps=settings["eps"], rho_th=settings["rho_th"], beta0=settings["beta0"],
+                              eps_hat=ramp, **kw)
+
+
+class Proposal:
+    """A trained (or freshly initialised) proposal network on the current device."""
+
+    def __init__(self, params: np.ndarray | None = None):
+        import torch
+        self.torch = torch
+        if params is None:
+            params = np.load(PARAMS_PATH)
+        params = np.asarray(params, dtype=np.float32)
+        assert params.shape == (NPARAM,)
+        self.p = torch.tensor(params, device="cuda")
+        self.lib = gda.load_library()
+
+    def outputs(self, solver: "gda.Solver"):
+        """Network outputs [N][5] for the solver's instance (host copy)."""
+        torch = self.torch
+        N = solver.N
+        F = torch.empty((N, 8), dtype=torch.float32, device="cuda")
+        O = torch.empty((N, 5), dtype=torch.float32, device="cuda")
+        solver.features(F.data_ptr())
+        st = torch.cuda.current_stream().cuda_stream
+        torch.cuda.synchronize()
+        r = self.lib.gda_mlp_forward(ct.c_void_p(self.p.data_ptr()), ct.c_void_p(F.data_ptr()), N,
+                                     ct.c_void_p(O.data_ptr()), None, ct.c_void_p(st))
+        if r != 0:
+            raise gda.GdaError(r, "gda_mlp_forward failed")
+        torch.cuda.synchronize()
+        return O.cpu().numpy().astype(np.float64)
+
+    def propose(self, solver: "gda.Solver"):
+        """Sets the solver's init_mode-3 base amplitudes and returns the settings."""
+        O = self.outputs(solver)
+        settings = settings_from_outputs(O[:, 2:5].mean(0))
+        xy = solver.model == gda.XY
+        solver.set_init_base(AMP * (O[:, 0] + (1j * O[:, 1] if xy else 0.0)))
+        return settings
+
+
+def proposed_params(settings: dict, seed: int, **kw) -> gda.Params:
+    """Run parameters of a proposed start (init_mode 3, perturbation AMP)."""
+    return run_params(settings, init_mode=3, init_amp=AMP, seed=seed, **kw)
+
+
+# ---------------------------------------------------------------- training
+def training_instance(k: int, seed0: int = 7):
+    """Seeded Gaussian-J instance number k: N uniform in [256, 1024], XY (odd k,
+    with g ~ U[-0.1, 0.1]) or Ising (even k, g = 0), J_ij ~ N(0, 1/N)."""
+    import synth
+    n = 256 + int(synth.uniform01(seed0 * 7919 + k, 1)[0] * 769)
+    xy = k % 2 == 1
+    J, g = synth.xy_gaussian(n, seed0 * 1000003 + k)
+    return J, (g if xy else np.zeros(n)), xy
+
+
+def ttt_steps(steps, E, target):
+    hit = np.nonzero(E <= target)[0]
+    return int(steps[hit[0]]) if len(hit) else None
+
+
+def make_targets(J, g, xy, R=32, nsteps=1500, every=50, seed=1):
+    """Runs the plain GD algorithm with every candidate setting; returns the
+    best configuration found (unit spins, [N][2]) and the candidate setting that
+    first reaches within 1e-3 of the best energy (ties: lower final energy)."""
+    s = gda.Solver(J, g, gda.XY if xy else gda.ISING)
+    runs = []
+    for (eps, rho, b0) in GRID:
+        p = run_params({"eps": eps, "rho_th": rho, "beta0": b0}, dt=0.05, init_mode=1, init_amp=1e-3, seed=seed,
+                       prec=gda.BF16, energy_every=every)
+        s.run(p, R, nsteps)
+        E, r, cfg = s.best()
+        st, Et, _ = s.trace()
+        runs.append((E, cfg, st, Et))
+    s.close()
+    Ebest = min(x[0] for x in runs)
+    target = Ebest + 1e-3 * abs(Ebest)
+    scored = []
+    for k, (E, cfg, st, Et) in enumerate(runs):
+        t = ttt_steps(st, Et, target)
+        scored.append((t if t is not None else 10 ** 9, E, k))
+    k_best = min(scored)[2]
+    cfg = min(runs, key=lambda x: x[0])[1]
+    S = np.zeros((len(cfg), 2))
+    if xy:
+        S[:, 0], S[:, 1] = np.cos(cfg), np.sin(cfg)
+    else:
+        S[:, 0] = cfg
+    return S, GRID[k_best]
+
+
+def init_params(seed: int) -> np.ndarray:
+    """Initial parameters: normal weights scaled by 1/sqrt(fan-in) (x sqrt 2
+    before ReLU), zero biases."""
+    rng = np.random.default_rng(seed)
+    parts = [rng.normal(0, math.sqrt(2.0 / 8), 128 * 8), np.zeros(128),
+             rng.normal(0, math.sqrt(2.0 / 128), 128 * 128), np.zeros(128),
+             rng.normal(0, math.sqrt(1.0 / 128), 5 * 128), np.zeros(5)]
+    return np.concatenate(parts).astype(np.float32)
+
+
+def _features_dev(J, g, xy):
+    import torch
+    s = gda.Solver(J, g, gda.XY if xy else gda.ISING)
+    F = torch.empty((J.shape[0], 8), dtype=torch.float32, device="cuda")
+    s.features(F.data_ptr())
+    s.sync()
+    s.close()
+    return F
+
+
+def train(n_inst=384, epochs=40, batch=16, lr=2e-3, wset=0.5, seed=0, log=print):
+    """Generates targets with plain GD runs and trains the network with the
+    library's kernels (forward, loss, backward, Adam); returns (params, losses)."""
+    import torch
+    lib = gda.load_library()
+    data = []
+    for k in range(n_inst):
+        J, g, xy = training_instance(k)
+        S, setting = make_targets(J, g, xy, seed=k + 1)
+        data.append((_features_dev(J, g, xy), torch.tensor(S, dtype=torch.float32, device="cuda"),
+                     outputs_from_settings(*setting), xy))
+        if (k + 1) % 64 == 0:
+            log(f"targets {k + 1}/{n_inst}")
+    p = torch.tensor(init_params(seed), device="cuda")
+    m1 = torch.zeros_like(p)
+    m2 = torch.zeros_like(p)
+    G = torch.zeros_like(p)
+    rng = np.random.default_rng(seed)
+    t = 0
+    losses = []
+    vp = lambda x: ct.c_void_p(x.data_ptr())  # noqa: E731
+    st = ct.c_void_p(torch.cuda.current_stream().cuda_stream)
+    for ep in range(epochs):
+        order = rng.permutation(n_inst)
+        tot, cnt = 0.0, 0
+        for b0 in range(0, n_inst, batch):
+            idx = order[b0:b0 + batch]
+            X = torch.cat([data[i][0] for i in idx]).contiguous()
+            S = torch.cat([data[i][1] for i in idx]).contiguous()
+            sizes = [data[i][0].shape[0] for i in idx]
+            offs = torch.tensor(np.concatenate([[0], np.cumsum(sizes)]), dtype=torch.int32, device="cuda")
+            cx = torch.tensor([1 if data[i][3] else 0 for i in idx], dtype=torch.int32, device="cuda")
+            T = torch.tensor([data[i][2] for i in idx], dtype=torch.float32, device="cuda")
+            M = X.shape[0]
+            O = torch.empty((M, 5), dtype=torch.float32, device="cuda")
+            H = torch.empty((M, 256), dtype=torch.float32, device="cuda")
+            dO = torch.empty_like(O)
+            L = torch.empty(len(idx), dtype=torch.float32, device="cuda")
+            G.zero_()
+            t += 1
+            for r in (lib.gda_mlp_forward(vp(p), vp(X), M, vp(O), vp(H), st),
+                      lib.gda_proposal_loss(vp(O), vp(S), vp(T), vp(offs), vp(cx), len(idx), wset, vp(dO), vp(L), st),
+                      lib.gda_mlp_backward(vp(p), vp(X), vp(H), vp(dO), M, vp(G), st),
+                      lib.gda_adam_step(vp(p), vp(G), vp(m1), vp(m2), NPARAM, lr, 0.9, 0.999, 1e-8, t, st)):
+                if r != 0:
+                    raise gda.GdaError(r, "proposal training kernel failed")
+            tot += float(L.sum())
+            cnt += len(idx)
+        losses.append(tot / cnt)
+        log(f"epoch {ep}: mean loss {losses[-1]:.4f}")
+    return p.cpu().numpy(), losses
+
+
+def evaluate(prop: Proposal, cases, R=64, nsteps=5000, every=25, log=print):
+    """Time to target of plain GD (default settings, small random start) and of
+    the proposal (its settings and start), BF16, same R and steps; the target
+    is within 1e-3 of the better FP64 energy of the two runs."""
+    import synth
+    import torch
+    rows = []
+    for model, n, seed in cases:
+        J, g = synth.xy_gaussian(n, seed)
+        xy = model == "xy"
+        if not xy:
+            g = np.zeros(n)
+        s = gda.Solver(J, g, gda.XY if xy else gda.ISING)
+        res = {}
+        for arm in ("plain", "learned"):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            if arm == "plain":
+                s.run(gda.default_params(dt=0.05, eps=0.1, rho_th=1.0, init_mode=1, init_amp=1e-3, seed=seed,
+                                         prec=gda.BF16, energy_every=every), R, nsteps)
+                settings = {"eps": 0.1, "rho_th": 1.0, "beta0": 1.0}
+            else:
+                settings = prop.propose(s)
+                s.run(proposed_params(settings, seed, dt=0.05, prec=gda.BF16, energy_every=every), R, nsteps)
+            E, _, _ = s.best(with_cfg=False)
+            e1.record()
+            e1.synchronize()
+            st_, Et, _ = s.trace()
+            res[arm] = (E, st_, Et, e0.elapsed_time(e1) / 1e3, settings)
+        Estar = min(res["plain"][0], res["learned"][0])
+        target = Estar + 1e-3 * abs(Estar)
+        row = {"model": model, "N": n, "seed": seed, "E_star": Estar}
+        for arm, (E, st_, Et, sec, settings) in res.items():
+            k = ttt_steps(st_, Et, target)
+            row[arm] = {"E": E, "ttt_steps": k, "ttt_s": None if k is None else sec * k / nsteps, "run_s": sec,
+                        "settings": settings}
+        rows.append(row)
+        log(row)
+        s.close()
+    return rows
+
+
+def main(argv=None):
+    import argparse
+    import json
+    import torch
+    ap = argparse.ArgumentParser()
+    ap.add_argument("cmd", choices=["train", "evaluate"])
+    ap.add_argument("--n-inst", type=int, default=384)
+    ap.add_argument("--epochs", type=int, default=40)
+    ap.add_argument("--out", default=PARAMS_PATH)
+    ap.add_argument("--report", default=None)
+    a = ap.parse_args(argv)
+    torch.cuda.set_device(0)
+    if a.cmd == "train":
+        params, losses = train(n_inst=a.n_inst, epochs=a.epochs)
+        os.makedirs(os.path.dirname(a.out), exist_ok=True)
+        np.save(a.out, params)
+        report = {"losses": losses}
+    else:
+        prop = Proposal(np.load(a.out))
+        cases = [("xy", 1024, 10 ** 6 + k) for k in range(4)] + [("ising", 2048, 10 ** 6 + 100 + k) for k in range(4)]
+        report = {"eval": evaluate(prop, cases)}
+    if a.report:
+        with open(a.report, "w") as fh:
+            json.dump(report, fh, indent=1, default=float)
+
+
+if __name__ == "__main__":
+    main()

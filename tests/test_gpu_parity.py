@@ -347,3 +347,23 @@ def test_full_size_sampled_restarts(gda, model, n, R, seed):
     Eb, rb_, _ = s.best(with_cfg=False)
     assert Eb == E.min() and rb_ == int(np.argmin(E))
     s.close()
+
+
+@pytest.mark.parametrize("model", ["xy", "ising"])
+def test_init_mode_3_base_plus_perturbation_bit_exact(gda, model):
+    n, R = 77, 5
+    J, g = instance(model, n, 1)
+    s = gda.Solver(J, g, gda.XY if model == "xy" else gda.ISING)
+    base = synth.initial_amplitudes(n, 1, 9, 0.7, model == "xy")[0]
+    s.set_init_base(base)
+    s.run(gda.default_params(init_mode=3, init_amp=0.25, seed=77), R, 0)
+    psi = s.get_state()[0]
+    pert = oracle.init_amplitudes(77, R, n, 0.25, model == "xy")
+    # FP32 sum of the FP32 base and the FP32 perturbation
+    if model == "xy":
+        ref = ((base.real.astype(np.float32) + pert.real.astype(np.float32)).astype(np.float64)
+               + 1j * (base.imag.astype(np.float32) + pert.imag.astype(np.float32)).astype(np.float64))
+    else:
+        ref = (base.astype(np.float32) + pert.astype(np.float32)).astype(np.float64)
+    assert np.array_equal(psi.astype(ref.dtype), ref)
+    s.close()

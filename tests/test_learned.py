@@ -1,0 +1,130 @@
+"""Learned proposal: the CUDA feature, forward, backward, loss and Adam kernels
+against the FP64 oracle, and training on the GPU."""
+import ctypes as ct
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import mlp_oracle as mo
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+
+    import __graft_entry__
+    assert torch.cuda.is_available()
+    __graft_entry__.build()
+    from paper_1807_00699_gb300 import gda
+    return torch, gda, gda.load_library()
+
+
+def vp(x):
+    return ct.c_void_p(x.data_ptr())
+
+
+def _st(torch):
+    return ct.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+@pytest.mark.parametrize("model,n", [("xy", 300), ("ising", 257), ("ising", 2)])
+def test_features_match_oracle(env, model, n):
+    torch, gda, lib = env
+    J, g = synth.xy_gaussian(n, 5)
+    if model == "ising":
+        g = np.zeros(n)
+    J = J.copy()
+    np.fill_diagonal(J, 0.7)  # the diagonal is excluded from the features
+    s = gda.Solver(J, g, gda.XY if model == "xy" else gda.ISING)
+    F = torch.empty((n, 8), dtype=torch.float32, device="cuda")
+    s.features(F.data_ptr())
+    s.sync()
+    ref = mo.features(J, g, model == "xy")
+    assert np.allclose(F.cpu().numpy(), ref, rtol=2e-5, atol=2e-6)
+    s.close()
+
+
+def test_forward_backward_match_oracle(env):
+    torch, gda, lib = env
+    M = 300  # three blocks, the last one ragged
+    p = (mo.init_params(1) + 0.05 * np.random.default_rng(2).normal(size=mo.NPARAM)).astype(np.float32)
+    X = np.random.default_rng(3).normal(size=(M, 8)).astype(np.float32)
+    dO = np.random.default_rng(4).normal(size=(M, 5)).astype(np.float32)
+    pd, Xd, dOd = (torch.tensor(a, device="cuda") for a in (p, X, dO))
+    O = torch.empty((M, 5), device="cuda")
+    H = torch.empty((M, 256), device="cuda")
+    G = torch.zeros(mo.NPARAM, device="cuda")
+    assert lib.gda_mlp_forward(vp(pd), vp(Xd), M, vp(O), vp(H), _st(torch)) == 0
+    assert lib.gda_mlp_backward(vp(pd), vp(Xd), vp(H), vp(dOd), M, vp(G), _st(torch)) == 0
+    torch.cuda.synchronize()
+    Oref, cache = mo.forward(p.astype(np.float64), X.astype(np.float64))
+    assert np.allclose(O.cpu().numpy(), Oref, rtol=1e-4, atol=1e-4 * np.abs(Oref).max())
+    assert np.allclose(H.cpu().numpy()[:, :128], cache[2], rtol=1e-4, atol=1e-4 * cache[2].max())
+    Gref = mo.backward(p.astype(np.float64), cache, dO.astype(np.float64))
+    Gg = G.cpu().numpy()
+    assert np.abs(Gg - Gref).max() < 1e-3 * np.abs(Gref).max()
+
+
+def test_loss_and_adam_match_oracle(env):
+    torch, gda, lib = env
+    rng = np.random.default_rng(7)
+    offs = [0, 40, 105, 300]
+    cplx = [1, 0, 1]
+    M = offs[-1]
+    O = rng.normal(size=(M, 5)).astype(np.float32)
+    S = np.zeros((M, 2))
+    th = rng.uniform(0, 2 * np.pi, M)
+    S[:, 0], S[:, 1] = np.cos(th), np.sin(th)
+    S[40:105, 0], S[40:105, 1] = np.sign(rng.normal(size=65)), 0.0
+    T = rng.normal(size=(3, 3)).astype(np.float32)
+    Od, Sd, Td = (torch.tensor(a, dtype=torch.float32, device="cuda") for a in (O, S, T))
+    offd = torch.tensor(offs, dtype=torch.int32, device="cuda")
+    cxd = torch.tensor(cplx, dtype=torch.int32, device="cuda")
+    dO = torch.empty_like(Od)
+    L = torch.empty(3, device="cuda")
+    assert lib.gda_proposal_loss(vp(Od), vp(Sd), vp(Td), vp(offd), vp(cxd), 3, 0.5, vp(dO), vp(L), _st(torch)) == 0
+    torch.cuda.synchronize()
+    dref, Lref = mo.proposal_loss(O.astype(np.float64), S, T.astype(np.float64), offs, cplx, 0.5)
+    assert np.allclose(L.cpu().numpy(), Lref, rtol=1e-5)
+    assert np.allclose(dO.cpu().numpy(), dref, rtol=1e-4, atol=1e-6)
+    # Adam, three steps
+    P = 1000
+    p = rng.normal(size=P).astype(np.float32)
+    pd = torch.tensor(p, device="cuda")
+    m1 = torch.zeros(P, device="cuda")
+    m2 = torch.zeros(P, device="cuda")
+    q, a1, a2 = p.astype(np.float64), np.zeros(P), np.zeros(P)
+    for t in (1, 2, 3):
+        gr = rng.normal(size=P).astype(np.float32)
+        gd = torch.tensor(gr, device="cuda")
+        assert lib.gda_adam_step(vp(pd), vp(gd), vp(m1), vp(m2), P, 0.01, 0.9, 0.999, 1e-8, t, _st(torch)) == 0
+        q, a1, a2 = mo.adam_step(q, gr.astype(np.float64), a1, a2, 0.01, 0.9, 0.999, 1e-8, t)
+    torch.cuda.synchronize()
+    assert np.allclose(pd.cpu().numpy(), q, rtol=1e-5, atol=1e-6)
+
+
+def test_short_training_reduces_loss(env):
+    torch, gda, lib = env
+    from paper_1807_00699_gb300 import proposal
+    _, losses = proposal.train(n_inst=8, epochs=12, batch=4, lr=3e-3, log=lambda *a: None)
+    assert losses[-1] < 0.7 * losses[0]
+
+
+def test_trained_proposal_gain_over_plain(env):
+    # The committed network against the plain algorithm (default settings,
+    # small random start) on held-out seeds; FP64 energies decide.
+    torch, gda, lib = env
+    from paper_1807_00699_gb300 import proposal
+    prop = proposal.Proposal()
+    rows = proposal.evaluate(prop, [("ising", 2048, 10 ** 6 + 200), ("xy", 1024, 10 ** 6 + 201)], R=64, nsteps=1500,
+                             log=lambda *a: None)
+    ising, xy = rows
+    # Ising: the learned settings and start reach a lower energy than the plain run
+    assert ising["learned"]["E"] < ising["plain"]["E"] - 0.01 * abs(ising["plain"]["E"])
+    assert ising["learned"]["ttt_steps"] is not None
+    # XY: the gain is not significant (held-out evaluation: faster on 2 of 4
+    # seeds at 5000 steps, about equal mean energy); require no loss beyond 1 %
+    assert xy["learned"]["E"] <= xy["plain"]["E"] + 0.01 * abs(xy["plain"]["E"])
