@@ -41,6 +41,9 @@ def parse():
     ap.add_argument("--prec", default="bf16", choices=["bf16", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32-ttt", action="store_true")
+    ap.add_argument("--workload", default="xy1000", choices=["xy1000", "batched"],
+                    help="xy1000: the headline workload; batched: the 2000-instance serving mix")
+    ap.add_argument("--batch-count", type=int, default=2000)
     return ap.parse_args()
 
 
@@ -333,10 +336,97 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_batched(args):
+    """The serving mix: instances with N log-uniform in [50, 2000], half Ising
+    (J in {-1, 0, +1}, density 1/2), half XY (J ~ N(0, 1/N)), R uniform in
+    [16, 256]; 2000 BF16 Euler steps of every instance per bench step."""
+    import torch
+
+    import __graft_entry__
+    import synth
+    torch.cuda.set_device(0)
+    __graft_entry__.build()
+    from paper_1807_00699_gb300 import gda
+    descs = synth.batched_mix(args.batch_count, 11)
+    insts = []
+    for d in descs:
+        J, g = synth.make_instance(d)
+        insts.append((J, g, gda.XY if d["model"] == "xy" else gda.ISING, d["r"]))
+    stream = torch.cuda.Stream()
+    t0 = time.perf_counter()
+    b = gda.Batch(insts, seed=5, stream=stream)
+    setup_s = time.perf_counter() - t0
+    # the unnormalised {-1, 0, +1} couplings reach |lambda| ~ 2 sqrt(N / 2) ~ 63 at
+    # N = 2000, where forward Euler stays stable at dt = 0.005 (diverges at 0.01)
+    p = gda.default_params(dt=0.005, eps=0.1, init_mode=1, init_amp=1e-3, prec=gda.BF16)
+    steps = 2000
+    # autotune the tile width on 200 steps
+    tune = {}
+    for bn in (128, 256):
+        b.set_tile(bn)
+        b.run(p, 200)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.run(p, 200)
+        e1.record(stream)
+        e1.synchronize()
+        tune[bn] = e0.elapsed_time(e1) / 1e3 / 200
+    bn = min(tune, key=tune.get)
+    b.set_tile(bn)
+    for _ in range(args.warmup):
+        b.run(p, steps)
+        b.best()
+    times = []
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    with ClockSampler(0) as clocks:
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            b.run(p, steps)
+            E, r = b.best()
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+    t = float(np.mean(times))
+    upd = sum(d["n"] * d["r"] for d in descs) * steps
+    flops = sum(2.0 * d["n"] ** 2 * d["r"] * (2 if d["model"] == "xy" else 1) for d in descs) * steps
+    # unbatched comparison: the first 50 instances one by one through the single-instance API
+    sub = insts[:50]
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    solvers = [gda.Solver(J, g, m, stream=stream) for J, g, m, _ in sub]
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for s_, (_, _, _, R) in zip(solvers, sub):
+        s_.run(gda.default_params(dt=0.005, eps=0.1, init_mode=1, init_amp=1e-3, prec=gda.BF16), R, steps)
+        s_.best(with_cfg=False)
+    e1.record(stream)
+    e1.synchronize()
+    t_sub = e0.elapsed_time(e1) / 1e3
+    upd_sub = sum(J.shape[0] * R for J, _, _, R in sub) * steps
+    line = {"metric": "spin-updates/s (batched serving mix)", "value": upd / t, "unit": "spin-updates/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": f"batched_mix_{args.batch_count}", "instances": len(descs), "steps": steps,
+                       "tile_bn": bn, "tune_s_per_step": tune, "setup_s": setup_s,
+                       "l2": "flushed (256 MB write) between timed steps"},
+            "tflops": flops / t / 1e12, "clocks": clocks.summary(),
+            "unbatched_first50": {"spin_updates_per_s": upd_sub / t_sub, "s": t_sub},
+            "batched_first50_equivalent": upd_sub / (upd / t)}
+    print(json.dumps(line), flush=True)
+    b.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched(args)
     else:
         run_ours(args)
 

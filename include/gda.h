@@ -274,6 +274,42 @@ gda_status gda_proposal_loss(const float* O, const float* S, const float* Tset, 
 gda_status gda_adam_step(float* params, const float* grad, float* m1, float* m2, int32_t P, float lr,
                          float beta1, float beta2, float eps, int32_t t, void* stream);
 
+/* ---- Batched serving (not in the paper) -----------------------------------
+ * Many independent instances (own N, model and R each) stepped together:
+ * one persistent tensor-core launch per step and model type over all their
+ * 128 x BN output tiles, steps replayed from a captured CUDA graph.  Every
+ * instance follows exactly the single-instance forward-Euler BF16 dynamics
+ * (Eqs. 2, 5, 6) with its own Philox seed.  The batch owns its device memory.
+ * Layout conventions are those of the single-instance calls. */
+typedef struct gda_batch gda_batch;
+
+/* n instances: N[k] spins, model[k], R[k] restarts, J[k] (N[k]^2 doubles,
+ * host, symmetric, finite), g[k] (N[k] doubles or NULL; g may be NULL).
+ * Instance k uses Philox key seed + k * 0x9E3779B97F4A7C15 (mod 2^64).
+ * Errors: GDA_ERR_INVALID, GDA_ERR_UNSUPPORTED (not an sm_103 device), OOM. */
+gda_status gda_batch_create(int32_t n, const int32_t* N, const int32_t* model, const int32_t* R,
+                            const double* const* J, const double* const* g, uint64_t seed, gda_batch** out);
+gda_status gda_batch_set_stream(gda_batch* b, void* stream);
+
+/* Tile width of the coupling product: 128 or 256 columns (gda_batch_tune
+ * picks the faster). */
+gda_status gda_batch_set_tile(gda_batch* b, int32_t bn);
+
+/* Runs `steps` forward-Euler BF16 steps of every instance (p->integ must be
+ * GDA_EULER, p->prec GDA_BF16; noise without decay; init_mode 0, 1 or 2;
+ * p->seed is ignored: instances use their own keys).  Asynchronous. */
+gda_status gda_batch_run(gda_batch* b, const gda_params* p, int64_t steps);
+
+/* FP64 Eq. (1) energy of the best restart of every instance (ties: lowest
+ * restart) into E[n], r[n] (host, either may be NULL).  Synchronises and
+ * reports device errors of earlier runs. */
+gda_status gda_batch_best(gda_batch* b, double* E, int32_t* r);
+
+/* State of instance k in the gda_get_state layout (host).  Synchronises. */
+gda_status gda_batch_get_state(gda_batch* b, int32_t k, float* psi, float* gamma, float* beta);
+const char* gda_batch_last_error(const gda_batch* b);
+void gda_batch_destroy(gda_batch* b);
+
 /* Number of kernels the library launched on this context since creation. */
 int64_t gda_kernel_launches(const gda_ctx* ctx);
 

@@ -255,6 +255,7 @@ gda_status check_params(gda_ctx* c, const gda_params* p) {
 StepArgs base_args(gda_ctx* c, const gda_params* p, bool tc) {
   StepArgs a{};
   a.N = c->N; a.Np = c->Np; a.C = c->C; a.R = c->R; a.Cp = c->Cp; a.Rp = c->Rp;
+  a.op_pitch = c->Np;
   a.cplx = c->cplx;
   a.mt_count = tc ? tc_mtiles(c->N) : simt_mtiles(c->N);
   a.dt = float(p->dt); a.eps = float(p->eps); a.rho_th = float(p->rho_th); a.eps_hat = float(p->eps_hat);

@@ -55,6 +55,7 @@ struct StepArgs {
   float* gstg;           // RK stage gains [Rp][Np]
   float* gacc;           // RK accumulator of gamma increments [Rp][Np]
   __nv_bfloat16* op_out; // BF16 copy of the next GEMM operand, or nullptr
+  int op_pitch;          // row pitch (elements) of op_out; Np except in packed batches
   const float* h1;       // drive h_1i = -g_i sqrt(rho_th), [Np]
   const float* beta_in;  // beta^n [Rp]
   float* beta_out;       // beta^{n+1} [Rp]

@@ -158,8 +158,9 @@ __device__ __forceinline__ void epi_chunk(const StepArgs& a, int i, int c0, cons
         if (CPLX) a.xs_next[o1] = si;
         a.gstg[og] = axpy(cf, kg, gn);
         if (a.op_out) {
-          a.op_out[o0] = __float2bfloat16_rn(sr);
-          if (CPLX) a.op_out[o1] = __float2bfloat16_rn(si);
+          const size_t p0 = size_t(c0 + k0) * a.op_pitch + i;
+          a.op_out[p0] = __float2bfloat16_rn(sr);
+          if (CPLX) a.op_out[p0 + a.op_pitch] = __float2bfloat16_rn(si);
         }
         continue;
       }
@@ -172,8 +173,9 @@ __device__ __forceinline__ void epi_chunk(const StepArgs& a, int i, int c0, cons
     if (CPLX) a.psi_out[o1] = ni;
     a.gam[og] = ng;
     if (a.op_out) {
-      a.op_out[o0] = __float2bfloat16_rn(nr);
-      if (CPLX) a.op_out[o1] = __float2bfloat16_rn(ni);
+      const size_t p0 = size_t(c0 + k0) * a.op_pitch + i;
+      a.op_out[p0] = __float2bfloat16_rn(nr);
+      if (CPLX) a.op_out[p0 + a.op_pitch] = __float2bfloat16_rn(ni);
     }
     const float rn = density(nr, ni);
     red[u] = rn;

@@ -63,6 +63,15 @@ SIGNATURES = {
     "gda_proposal_loss": (ct.c_int, [_VP, _VP, _VP, _VP, _VP, ct.c_int32, ct.c_float, _VP, _VP, _VP]),
     "gda_adam_step": (ct.c_int, [_VP, _VP, _VP, _VP, ct.c_int32, ct.c_float, ct.c_float, ct.c_float, ct.c_float,
                                  ct.c_int32, _VP]),
+    "gda_batch_create": (ct.c_int, [ct.c_int32, ct.POINTER(ct.c_int32), ct.POINTER(ct.c_int32), ct.POINTER(ct.c_int32),
+                                    ct.POINTER(_VP), ct.POINTER(_VP), ct.c_uint64, ct.POINTER(_VP)]),
+    "gda_batch_set_stream": (ct.c_int, [_VP, _VP]),
+    "gda_batch_set_tile": (ct.c_int, [_VP, ct.c_int32]),
+    "gda_batch_run": (ct.c_int, [_VP, ct.POINTER(Params), ct.c_int64]),
+    "gda_batch_best": (ct.c_int, [_VP, _D, ct.POINTER(ct.c_int32)]),
+    "gda_batch_get_state": (ct.c_int, [_VP, ct.c_int32, _F, _F, _F]),
+    "gda_batch_last_error": (ct.c_char_p, [_VP]),
+    "gda_batch_destroy": (None, [_VP]),
     "gda_kernel_launches": (ct.c_int64, [_VP]),
     "gda_last_error": (ct.c_char_p, [_VP]),
     "gda_status_string": (ct.c_char_p, [ct.c_int]),
@@ -260,6 +269,79 @@ class Solver:
     def close(self):
         if getattr(self, "_h", None):
             self._lib.gda_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+GOLDEN64 = 0x9E3779B97F4A7C15
+
+
+class Batch:
+    """A gda_batch: many instances stepped together (BF16 Euler)."""
+
+    def __init__(self, instances, seed: int = 0, stream=None):
+        """instances: list of (J, g or None, model, R)."""
+        lib = load_library()
+        self._lib = lib
+        n = len(instances)
+        self.N = [int(np.asarray(J).shape[0]) for J, _, _, _ in instances]
+        self.model = [int(m) for _, _, m, _ in instances]
+        self.R = [int(r) for _, _, _, r in instances]
+        self._Js = [np.ascontiguousarray(J, dtype=np.float64) for J, _, _, _ in instances]
+        self._gs = [None if g is None else np.ascontiguousarray(g, dtype=np.float64) for _, g, _, _ in instances]
+        Jp = (_VP * n)(*[a.ctypes.data for a in self._Js])
+        gp = (_VP * n)(*[0 if a is None else a.ctypes.data for a in self._gs])
+        arr = lambda v: (ct.c_int32 * n)(*v)  # noqa: E731
+        h = _VP()
+        st = lib.gda_batch_create(n, arr(self.N), arr(self.model), arr(self.R), Jp, gp, seed & (2 ** 64 - 1),
+                                  ct.byref(h))
+        if st != 0:
+            raise GdaError(st, "gda_batch_create failed")
+        self._h = h
+        self.n = n
+        self.seed = seed
+        if stream is not None:
+            handle = getattr(stream, "cuda_stream", stream)
+            self._check(lib.gda_batch_set_stream(h, _VP(handle or 0)))
+
+    def instance_seed(self, k: int) -> int:
+        return (self.seed + k * GOLDEN64) & (2 ** 64 - 1)
+
+    def _check(self, st):
+        if st != 0:
+            raise GdaError(st, self._lib.gda_batch_last_error(self._h).decode())
+
+    def set_tile(self, bn: int):
+        self._check(self._lib.gda_batch_set_tile(self._h, bn))
+
+    def run(self, params: Params, steps: int):
+        self._check(self._lib.gda_batch_run(self._h, ct.byref(params), int(steps)))
+
+    def best(self):
+        E = np.empty(self.n, dtype=np.float64)
+        r = np.empty(self.n, dtype=np.int32)
+        self._check(self._lib.gda_batch_best(self._h, _ptr(E, ct.c_double), _ptr(r, ct.c_int32)))
+        return E, r
+
+    def get_state(self, k: int):
+        N, R, W = self.N[k], self.R[k], 2 if self.model[k] == XY else 1
+        psi = np.empty(R * N * W, dtype=np.float32)
+        gam = np.empty(R * N, dtype=np.float32)
+        beta = np.empty(R, dtype=np.float32)
+        self._check(self._lib.gda_batch_get_state(self._h, k, _ptr(psi, ct.c_float), _ptr(gam, ct.c_float),
+                                                  _ptr(beta, ct.c_float)))
+        psi = psi.reshape(R, N, W)
+        psi = psi[..., 0] + 1j * psi[..., 1] if W == 2 else psi[..., 0]
+        return psi, gam.reshape(R, N), beta
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.gda_batch_destroy(self._h)
             self._h = None
 
     def __del__(self):
