@@ -63,7 +63,13 @@ typedef enum { GDA_EULER = 0, GDA_RK4 = 1 } gda_integrator;
 
 typedef enum {
   GDA_FP32 = 0, /* J.Psi on CUDA cores in FP32 (the plain reference path)     */
-  GDA_BF16 = 1  /* J.Psi on tcgen05 tensor cores, BF16 operands, FP32 accum   */
+  GDA_BF16 = 1, /* J.Psi on tcgen05 tensor cores, BF16 operands, FP32 accum   */
+  GDA_FP8 = 2   /* J.Psi on tcgen05 tensor cores, E4M3 operands, FP32 accum:
+                 * J0_ij stored as e4m3(J0_ij / s_i), s_i = max_j |J0_ij| / 448
+                 * (row scale), amplitudes as e4m3(psi * 64) (|psi| up to 7
+                 * before saturation), Y_i = acc_i * s_i / 64.  Per-step
+                 * schedule only; the energy tracking of energy_every uses
+                 * the BF16 product of the projected spins. */
 } gda_precision;
 
 /* Run parameters (Eqs. 2, 5, 6; Sec. 2 integrator).  Fill with
@@ -172,7 +178,8 @@ gda_status gda_trace(gda_ctx* ctx, int64_t* step, double* E, int32_t* r, int32_t
 
 /* The coupling product alone (the GEMM of Eq. 2's sum over j != i):
  * Y = J0 X for R restarts, with J0 = J minus its diagonal, through the
- * FP32 (prec = GDA_FP32) or tensor-core BF16 (GDA_BF16) path.  X, Y: host
+ * FP32 (prec = GDA_FP32), tensor-core BF16 (GDA_BF16) or tensor-core FP8
+ * (GDA_FP8) path.  X, Y: host
  * arrays in the psi layout of gda_get_state.  Replaces the context's state
  * (a following gda_run must start with init_mode 0 or 1).  Synchronises. */
 gda_status gda_coupling(gda_ctx* ctx, int32_t prec, int32_t R, const float* X, float* Y);

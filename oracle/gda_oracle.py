@@ -57,7 +57,7 @@ __all__ = [
     "energies", "project", "brute_force_ising", "philox4x32_10",
     "philox_generic", "philox_uniform", "box_muller", "noise_xi",
     "init_amplitudes", "rhs", "euler_step", "rk4_step", "add_noise",
-    "run", "round_bf16", "best_of", "field_drive",
+    "run", "round_bf16", "best_of", "field_drive", "round_e4m3", "fp8_coupling_scales",
 ]
 
 # --------------------------------------------------------------------------
@@ -85,7 +85,7 @@ class Params:
     init_mode: int = 1            # 0: psi = 0, 1: seeded U(-a, a) per component
     init_amp: float = 1e-3
     energy_every: int = 0         # record best energy every k steps (0: off)
-    operand: str = "fp64"         # 'fp64' or 'bf16' rounding of the J.Psi operands
+    operand: str = "fp64"         # 'fp64', 'bf16' or 'fp8' rounding of the J.Psi operands
 
     def with_(self, **kw) -> "Params":
         return replace(self, **kw)
@@ -293,6 +293,55 @@ def round_bf16(x: np.ndarray) -> np.ndarray:
     return b.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
+def _e4m3_table() -> np.ndarray:
+    """All finite non-negative E4M3 values (OCP FP8: 1 sign, 4 exponent bits
+    with bias 7, 3 mantissa bits, subnormals at exponent 0, largest 448, the
+    all-ones code is NaN), ascending, indexed by their 7-bit code."""
+    vals = []
+    for code in range(0x7F):
+        e, m = code >> 3, code & 7
+        vals.append((m / 8.0) * 2.0 ** -6 if e == 0 else (1 + m / 8.0) * 2.0 ** (e - 7))
+    return np.array(vals)
+
+
+_E4M3 = _e4m3_table()
+
+
+def round_e4m3(x: np.ndarray) -> np.ndarray:
+    """Round to E4M3 the way the device writes FP8 operands: FP64 -> FP32
+    (nearest even), then to the nearest E4M3 value with ties to the even code,
+    saturating at +-448 (satfinite).  Returns FP64 values."""
+    x = np.asarray(x, dtype=np.float32).astype(np.float64)
+    a = np.minimum(np.abs(x), 448.0)
+    hi = np.searchsorted(_E4M3, a, side="left").clip(0, len(_E4M3) - 1)
+    lo = (hi - 1).clip(0, None)
+    dl, dh = a - _E4M3[lo], _E4M3[hi] - a
+    pick = np.where(dl < dh, lo, np.where(dh < dl, hi, np.where(lo % 2 == 0, lo, hi)))
+    return np.sign(x) * _E4M3[pick]
+
+
+# Fixed scale of the FP8 amplitude operand: psi / FP8_PSI_SCALE is stored, so
+# amplitudes 2^-12 .. 7 stay within E4M3's range.
+FP8_PSI_SCALE = 1.0 / 64.0
+
+
+def fp8_coupling_scales(J0: np.ndarray) -> np.ndarray:
+    """Per-row scales of the FP8 coupling operand: s_i = max_j |J0_ij| / 448
+    (1 for an all-zero row), computed in FP32 like the device."""
+    m = np.abs(np.asarray(J0, dtype=np.float32)).max(axis=1).astype(np.float32)
+    return np.where(m > 0, (m / np.float32(448.0)).astype(np.float32), np.float32(1.0)).astype(np.float64)
+
+
+def fp8_coupling(J0: np.ndarray, X: np.ndarray) -> np.ndarray:
+    """Y = J0 X with FP8 operands: row-scaled E4M3 couplings times E4M3
+    amplitudes at the fixed scale, products summed exactly (FP64)."""
+    s = fp8_coupling_scales(J0)
+    J8 = round_e4m3(np.asarray(J0, dtype=np.float32) / s.astype(np.float32)[:, None])
+    X8 = round_e4m3(np.asarray(X) / FP8_PSI_SCALE) if not np.iscomplexobj(X) else \
+        round_e4m3(X.real / FP8_PSI_SCALE) + 1j * round_e4m3(X.imag / FP8_PSI_SCALE)
+    return (X8 @ J8.T) * (s[None, :] * FP8_PSI_SCALE)
+
+
 def field_drive(g: np.ndarray, rho_th: float) -> np.ndarray:
     """h_1i = -g_i sqrt(rho_th): the q=1 drive of Eq. (2) that makes the fixed
     point minimise Eq. (1)'s field term (Eq. 8 with g_i = -h_1i / sqrt(rho_th))."""
@@ -317,6 +366,8 @@ def rhs(psi, gamma, beta, J0, h1, p: Params, model: str):
     rho = np.real(psi * np.conj(psi))
     if p.operand == "bf16":
         Y = round_bf16(psi) @ round_bf16(J0).T
+    elif p.operand == "fp8":
+        Y = fp8_coupling(J0, psi)
     else:
         Y = psi @ J0.T                       # Y[r, i] = sum_j J0[i, j] psi[r, j]
     f = psi * (gamma - rho) + beta[:, None] * Y + h1[None, :]

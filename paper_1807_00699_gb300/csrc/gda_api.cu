@@ -34,6 +34,9 @@ struct gda_ctx {
   double* J64 = nullptr;  // [Np][Np], diagonal kept
   float* J32 = nullptr;   // [Np][Np], diagonal removed
   __nv_bfloat16* J16 = nullptr;
+  unsigned char* J8 = nullptr;  // [Np][Np] E4M3, row-scaled (FP8 path, on first use)
+  float* jscale = nullptr;      // [Np] row scales of J8
+  bool j8_ready = false;
   int* Jint = nullptr;
   double* g64 = nullptr;  // [Np]
   float* g32 = nullptr;   // [Np]
@@ -57,6 +60,8 @@ struct gda_ctx {
   float* rho[2] = {nullptr, nullptr};
   float* epart = nullptr;
   __nv_bfloat16* ops = nullptr;  // [3][Cp][Np]: operand ping-pong + projected spins
+  unsigned char* ops8 = nullptr;  // [2][Cp][Np]: E4M3 operand ping-pong (FP8 path)
+  TcPlan* plan8 = nullptr;
   double* S64 = nullptr;
   int* Sint = nullptr;
   double* part64 = nullptr;
@@ -139,6 +144,9 @@ void free_state(gda_ctx* c) {
   dfree(c->ops); dfree(c->S64); dfree(c->Sint); dfree(c->part64); dfree(c->partint); dfree(c->E64);
   if (c->plan) tc_plan_destroy(c->plan);
   c->plan = nullptr;
+  dfree(c->ops8);
+  if (c->plan8) tc_plan_destroy(c->plan8);
+  c->plan8 = nullptr;
   c->R = c->C = c->Cp = c->Rp = c->Rcap_cols = 0;
   c->have_state = false;
 }
@@ -227,6 +235,28 @@ gda_status load_instance(gda_ctx* c, const double* J, const double* g, cudaMemcp
     CK(dalloc(&c->partint, size_t(c->MT) * c->Rp));
   }
   LK(launch_prepare_J(c->J64, c->Np, c->J32, c->J16, c->int_exact ? c->Jint : nullptr, c->stream));
+  c->j8_ready = false;
+  return GDA_OK;
+}
+
+// FP8 operands on first use: row-scaled E4M3 couplings, the E4M3 operand
+// buffers of the current state and their tensor maps.
+gda_status ensure_fp8(gda_ctx* c) {
+  const size_t Np = c->Np;
+  if (!c->J8) {
+    CK(dalloc(&c->J8, Np * Np));
+    CK(dalloc(&c->jscale, Np));
+  }
+  if (!c->j8_ready) {
+    LK(launch_prepare_J8(c->J32, int(Np), c->J8, c->jscale, c->stream));
+    c->j8_ready = true;
+  }
+  if (!c->ops8) {
+    const size_t cn = size_t(c->Cp) * Np;
+    CK(dalloc(&c->ops8, 2 * cn));
+    CK(cudaMemsetAsync(c->ops8, 0, 2 * cn, c->stream));
+    CK(tc_plan8_create(&c->plan8, c->J8, int(Np), c->ops8, 2, c->Cp));
+  }
   return GDA_OK;
 }
 
@@ -235,7 +265,8 @@ bool finite(double x) { return std::isfinite(x); }
 gda_status check_params(gda_ctx* c, const gda_params* p) {
   if (!p) return fail(c, GDA_ERR_INVALID, "params is NULL");
   if (p->integ != GDA_EULER && p->integ != GDA_RK4) return fail(c, GDA_ERR_INVALID, "unknown integrator %d", p->integ);
-  if (p->prec != GDA_FP32 && p->prec != GDA_BF16) return fail(c, GDA_ERR_INVALID, "unknown precision %d", p->prec);
+  if (p->prec != GDA_FP32 && p->prec != GDA_BF16 && p->prec != GDA_FP8)
+    return fail(c, GDA_ERR_INVALID, "unknown precision %d", p->prec);
   const double v[] = {p->dt, p->eps, p->rho_th, p->gamma0, p->beta0, p->eps_hat, p->noise_D, p->init_amp};
   for (double x : v)
     if (!finite(x)) return fail(c, GDA_ERR_INVALID, "non-finite parameter");
@@ -247,8 +278,8 @@ gda_status check_params(gda_ctx* c, const gda_params* p) {
   if (p->energy_every < 0) return fail(c, GDA_ERR_INVALID, "energy_every must be >= 0");
   if (p->schedule < GDA_SCHEDULE_AUTO || p->schedule > GDA_SCHEDULE_RESIDENT)
     return fail(c, GDA_ERR_INVALID, "unknown schedule %d", p->schedule);
-  if (p->prec == GDA_BF16 && !c->tc_ok)
-    return fail(c, GDA_ERR_UNSUPPORTED, "BF16 tensor-core path needs an sm_103 device");
+  if (p->prec != GDA_FP32 && !c->tc_ok)
+    return fail(c, GDA_ERR_UNSUPPORTED, "tensor-core path needs an sm_103 device");
   return GDA_OK;
 }
 
@@ -273,7 +304,9 @@ StepArgs base_args(gda_ctx* c, const gda_params* p, bool tc) {
 }
 
 gda_status launch_step(gda_ctx* c, const StepArgs& a, bool tc, const float* operand32, int op_buf) {
-  if (tc) {
+  if (a.row_scale) {
+    LK(launch_step_tc8(c->plan8, a, op_buf, c->stream));
+  } else if (tc) {
     LK(launch_step_tc(c->plan, a, op_buf, c->stream));
   } else {
     LK(launch_step_simt(a, c->J32, operand32, c->stream));
@@ -369,7 +402,7 @@ int64_t gda_kernel_launches(const gda_ctx* c) { return c ? c->launches : 0; }
 void gda_destroy(gda_ctx* c) {
   if (!c) return;
   free_state(c);
-  dfree(c->J64); dfree(c->J32); dfree(c->J16); dfree(c->Jint); dfree(c->g64); dfree(c->g32); dfree(c->h1);
+  dfree(c->J64); dfree(c->J32); dfree(c->J16); dfree(c->J8); dfree(c->jscale); dfree(c->Jint); dfree(c->g64); dfree(c->g32); dfree(c->h1);
   dfree(c->d_flags); dfree(c->d_maxabs); dfree(c->d_diag);
   dfree(c->bestE); dfree(c->bestR); dfree(c->cfg8); dfree(c->cfgth);
   dfree(c->t_step); dfree(c->t_E); dfree(c->t_r); dfree(c->t_count); dfree(c->err); dfree(c->flags);
@@ -477,7 +510,8 @@ gda_status gda_run(gda_ctx* c, const gda_params* p, int32_t R, int64_t steps) {
   if (R < 1) return fail(c, GDA_ERR_INVALID, "R must be >= 1");
   if (steps < 0) return fail(c, GDA_ERR_INVALID, "steps must be >= 0");
   if (size_t(c->cplx ? 2 : 1) * size_t(R) > size_t(1) << 24) return fail(c, GDA_ERR_INVALID, "R too large");
-  const bool tc = p->prec == GDA_BF16;
+  const bool tc = p->prec != GDA_FP32;
+  const bool f8 = p->prec == GDA_FP8;
   if (p->init_mode == 2) {
     if (!c->have_state || c->R != R) return fail(c, GDA_ERR_STATE, "init_mode 2 needs a state with the same R");
   } else {
@@ -496,16 +530,26 @@ gda_status gda_run(gda_ctx* c, const gda_params* p, int32_t R, int64_t steps) {
   LK(launch_fill_h1(c->g64, c->g32, c->N, -1.0f, c->stream));
   const size_t cn = size_t(c->Cp) * c->Np;
   c->opcur = 0;
-  if (tc) LK(launch_to_bf16(c->psi[c->cur], c->ops, cn, c->stream));
+  if (f8) {
+    s = ensure_fp8(c);
+    if (s != GDA_OK) return s;
+    LK(launch_to_e4m3(c->psi[c->cur], c->ops8, cn, c->stream));
+  } else if (tc) {
+    LK(launch_to_bf16(c->psi[c->cur], c->ops, cn, c->stream));
+  }
   const bool decay = p->noise_D != 0.0 && p->noise_decay;
   c->rcur = 0;
   if (decay) LK(launch_rho_partials(tc, c->psi[c->cur], c->N, c->Np, c->R, c->Rp, c->cplx, c->rho[0], c->stream));
 
   StepArgs base = base_args(c, p, tc);
+  if (f8) {
+    base.row_scale = c->jscale;
+    base.op8_inv = 1.0f / kFp8PsiScale;
+  }
   const size_t opsz = cn;
   // Resident persistent kernel: BF16 Euler runs whose tiles all fit on the
   // device at once run as one launch per tracking segment.
-  const bool resident = tc && p->integ == GDA_EULER && p->schedule != GDA_SCHEDULE_PER_STEP &&
+  const bool resident = p->prec == GDA_BF16 && p->integ == GDA_EULER && p->schedule != GDA_SCHEDULE_PER_STEP &&
                         res_fits(c->N, c->C, c->dev) &&
                         (long long)((c->C + 127) / 128) * ((c->N + 127) / 128) <= kMaxResidentTiles;
   if (p->schedule == GDA_SCHEDULE_RESIDENT && !resident)
@@ -558,7 +602,8 @@ gda_status gda_run(gda_ctx* c, const gda_params* p, int32_t R, int64_t steps) {
       a.psi_n = c->psi[c->cur];
       a.xs = c->psi[c->cur];
       a.psi_out = c->psi[c->cur ^ 1];
-      a.op_out = tc ? c->ops + (c->opcur ^ 1) * opsz : nullptr;
+      a.op_out = (tc && !f8) ? c->ops + (c->opcur ^ 1) * opsz : nullptr;
+      a.op8_out = f8 ? c->ops8 + (c->opcur ^ 1) * opsz : nullptr;
       s = launch_step(c, a, tc, c->psi[c->cur], c->opcur);
       if (s != GDA_OK) return s;
       c->cur ^= 1;
@@ -573,7 +618,8 @@ gda_status gda_run(gda_ctx* c, const gda_params* p, int32_t R, int64_t steps) {
         a.xs_next = st < 3 ? xout[st] : nullptr;
         a.psi_out = c->psi[c->cur];
         const int in_buf = c->opcur ^ (st & 1);
-        a.op_out = tc ? c->ops + (in_buf ^ 1) * opsz : nullptr;
+        a.op_out = (tc && !f8) ? c->ops + (in_buf ^ 1) * opsz : nullptr;
+        a.op8_out = f8 ? c->ops8 + (in_buf ^ 1) * opsz : nullptr;
         s = launch_step(c, a, tc, xin[st], in_buf);
         if (s != GDA_OK) return s;
       }
@@ -753,20 +799,27 @@ gda_status gda_features(gda_ctx* c, float* F) {
 gda_status gda_coupling(gda_ctx* c, int32_t prec, int32_t R, const float* X, float* Y) {
   if (!c) return GDA_ERR_INVALID;
   if (!X || !Y || R < 1) return fail(c, GDA_ERR_INVALID, "X or Y NULL, or R < 1");
-  if (prec != GDA_FP32 && prec != GDA_BF16) return fail(c, GDA_ERR_INVALID, "unknown precision");
-  if (prec == GDA_BF16 && !c->tc_ok) return fail(c, GDA_ERR_UNSUPPORTED, "BF16 path needs an sm_103 device");
+  if (prec != GDA_FP32 && prec != GDA_BF16 && prec != GDA_FP8) return fail(c, GDA_ERR_INVALID, "unknown precision");
+  if (prec != GDA_FP32 && !c->tc_ok) return fail(c, GDA_ERR_UNSUPPORTED, "tensor-core path needs an sm_103 device");
   gda_status s = gda_set_state(c, X, nullptr, nullptr, R, 0);
   if (s != GDA_OK) return s;
-  const bool tc = prec == GDA_BF16;
+  const bool tc = prec != GDA_FP32;
   gda_params p;
   gda_default_params(&p);
   StepArgs a = base_args(c, &p, tc);
+  if (prec == GDA_FP8) {
+    s = ensure_fp8(c);
+    if (s != GDA_OK) return s;
+    a.row_scale = c->jscale;
+    LK(launch_to_e4m3(c->psi[0], c->ops8, size_t(c->Cp) * c->Np, c->stream));
+  } else if (tc) {
+    LK(launch_to_bf16(c->psi[0], c->ops, size_t(c->Cp) * c->Np, c->stream));
+  }
   a.mode = M_RAW;
   a.psi_n = c->psi[0];
   a.xs = c->psi[0];
   a.psi_out = c->stg[0];
   a.beta_in = c->beta[0];
-  if (tc) LK(launch_to_bf16(c->psi[0], c->ops, size_t(c->Cp) * c->Np, c->stream));
   s = launch_step(c, a, tc, c->psi[0], 0);
   if (s != GDA_OK) return s;
   const size_t rn = size_t(R) * c->N, W = c->cplx ? 2 : 1;

@@ -56,6 +56,9 @@ struct StepArgs {
   float* gacc;           // RK accumulator of gamma increments [Rp][Np]
   __nv_bfloat16* op_out; // BF16 copy of the next GEMM operand, or nullptr
   int op_pitch;          // row pitch (elements) of op_out; Np except in packed batches
+  unsigned char* op8_out;  // E4M3 copy of the next GEMM operand (FP8 path), or nullptr
+  float op8_inv;         // 1 / scale of the FP8 amplitude operand
+  const float* row_scale;  // FP8 path: Y_i = row_scale[i] * (J8 X8)_i, else nullptr
   const float* h1;       // drive h_1i = -g_i sqrt(rho_th), [Np]
   const float* beta_in;  // beta^n [Rp]
   float* beta_out;       // beta^{n+1} [Rp]
@@ -85,6 +88,16 @@ cudaError_t tc_plan_create(TcPlan** plan, const __nv_bfloat16* J16, int Np,
                            const __nv_bfloat16* ops, int n_op_bufs, int Cp);
 void tc_plan_destroy(TcPlan* plan);
 cudaError_t launch_step_tc(const TcPlan* plan, const StepArgs& a, int op_buf, cudaStream_t s);
+// FP8 operands (E4M3 J with per-row scales, E4M3 amplitudes at a fixed scale):
+// plan over J8 [Np][Np] and ops8 [n_op_bufs * Cp][Np] (bytes).
+cudaError_t tc_plan8_create(TcPlan** plan, const unsigned char* J8, int Np, const unsigned char* ops8, int n_op_bufs,
+                            int Cp);
+cudaError_t launch_step_tc8(const TcPlan* plan, const StepArgs& a, int op_buf, cudaStream_t s);
+constexpr float kFp8PsiScale = 1.0f / 64.0f;
+// J8_ij = e4m3(J32_ij / s_i), s_i = max_j |J32_ij| / 448 (1 for a zero row).
+cudaError_t launch_prepare_J8(const float* J32, int Np, unsigned char* J8, float* scale, cudaStream_t s);
+// y = e4m3(x / kFp8PsiScale), n elements.
+cudaError_t launch_to_e4m3(const float* x, unsigned char* y, size_t n, cudaStream_t s);
 int tc_mtiles(int N);
 int tc_pick_bn(int N, int C);
 bool tc_supported(int device);

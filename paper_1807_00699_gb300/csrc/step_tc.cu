@@ -1,323 +1,8 @@
-// Tensor-core GD step for sm_103a: Y = J0 X with tcgen05.mma (BF16 operands,
-// FP32 accumulator in tensor memory), both operands staged in shared memory by
-// TMA (cp.async.bulk.tensor, 128-byte swizzle, no multicast), fused with the
-// step epilogue of Eqs. (2), (5), (6).
-//
-// One CTA computes one 128 x BN tile of Y (spins x columns).  Warp roles:
-//   warp 0        TMA producer (one elected lane), STAGES-deep ring
-//   warp 1        TMEM allocator and MMA issuer (one elected lane)
-//   warps 2..9    epilogue: warp w reads TMEM lane quarter (w % 4), half of
-//                 the columns each, and runs the per-element update.
-// Every mbarrier wait is bounded by a clock budget; on expiry the CTA records
-// E_TIMEOUT, stops issuing work, drains what it issued and frees its TMEM.
-#include <cuda.h>
-
-#include <cstdio>
-
-#include "tc_epilogue.cuh"
-#include "tc_ptx.cuh"
+// BF16 instantiation of the tensor-core step kernel (step_tc.cuh) and the
+// tile-width choice shared by both precisions.
+#include "step_tc.cuh"
 
 namespace gda {
-
-namespace {
-
-using namespace ptx;
-constexpr int NTHREADS = 320;
-
-template <int BN, int STAGES>
-struct TcCfg {
-  static constexpr uint32_t A_BYTES = BM * BK * 2;
-  static constexpr uint32_t B_BYTES = BN * BK * 2;
-  static constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
-  static constexpr uint32_t TAIL = (2 * STAGES + 4) * 8 + 6 * BN * 4 + 16;
-  static constexpr uint32_t SMEM = 1024 + STAGES * STAGE_BYTES + TAIL;
-};
-
-// Persistent over output tiles: CTA b processes tiles b, b + gridDim.x, ...
-// (column block fastest), with two tensor-memory accumulators so that the
-// epilogue of one tile overlaps the MMAs of the next.
-template <int BN, int STAGES, bool CPLX, int MODE>
-__global__ void __launch_bounds__(NTHREADS, 1)
-    step_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int b_row0,
-                   StepArgs a) {
-  using Cfg = TcCfg<BN, STAGES>;
-  extern __shared__ uint8_t smem_raw[];
-  const uint32_t raw = smem_u32(smem_raw);
-  const uint32_t base = (raw + 1023u) & ~1023u;
-  uint8_t* smem = smem_raw + (base - raw);
-  const uint32_t sA = base;
-  const uint32_t sB = base + STAGES * Cfg::A_BYTES;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * Cfg::STAGE_BYTES);
-  float* s_beta = reinterpret_cast<float*>(bars + 2 * STAGES + 4);
-  float* s_dsc = s_beta + BN;
-  float* s_red = s_dsc + BN;  // [4][BN]
-  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(s_red + 4 * BN);
-  int* s_flag = reinterpret_cast<int*>(s_tmem + 1);  // [0] abort, [1] diverged
-
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int KB = (a.N + BK - 1) / BK;
-  const int NT = (a.C + BN - 1) / BN;
-  const int T = NT * ((a.N + BM - 1) / BM);
-  auto full_bar = [&](int s) { return smem_u32(bars + s); };
-  auto empty_bar = [&](int s) { return smem_u32(bars + STAGES + s); };
-  auto acc_full = [&](int b) { return smem_u32(bars + 2 * STAGES + b); };
-  auto acc_empty = [&](int b) { return smem_u32(bars + 2 * STAGES + 2 + b); };
-
-  if (threadIdx.x == 0) {
-    stamp(a, 0);
-    for (int s = 0; s < STAGES; ++s) {
-      mbar_init(full_bar(s), 1);
-      mbar_init(empty_bar(s), 1);
-    }
-    for (int b = 0; b < 2; ++b) {
-      mbar_init(acc_full(b), 1);
-      mbar_init(acc_empty(b), 1);
-    }
-    s_flag[0] = 0;
-    s_flag[1] = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  constexpr uint32_t TCOLS = 2 * BN <= 256 ? 256 : 512;  // power of two
-  if (warp == 1) tmem_alloc(smem_u32(s_tmem), TCOLS);
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = *s_tmem;
-  if (threadIdx.x == 0) stamp(a, 1);
-
-  if (warp == 0) {
-    // ---------------- TMA producer ----------------
-    if (lane == 0) {
-      int it = 0;
-      bool stop = false;
-      for (int t = blockIdx.x; t < T && !stop; t += gridDim.x) {
-        const int m0 = (t / NT) * BM, n0 = (t % NT) * BN;
-        for (int kb = 0; kb < KB; ++kb, ++it) {
-          const int s = it % STAGES;
-          const uint32_t ph = (it / STAGES) & 1;
-          if (!mbar_wait(empty_bar(s), ph ^ 1u) || *(volatile int*)&s_flag[0]) {
-            stop = true;
-            break;
-          }
-          mbar_arrive_expect_tx(full_bar(s), Cfg::STAGE_BYTES);
-          tma_load_2d(sA + s * Cfg::A_BYTES, &tmA, kb * BK, m0, full_bar(s));
-          tma_load_2d(sB + s * Cfg::B_BYTES, &tmB, kb * BK, b_row0 + n0, full_bar(s));
-        }
-      }
-      if (stop) {
-        atomicOr(&s_flag[0], 1);
-        for (int k = it - 1; k >= 0 && k >= it - STAGES; --k) (void)mbar_wait(full_bar(k % STAGES), (k / STAGES) & 1);
-      }
-    }
-  } else if (warp == 1) {
-    // ---------------- MMA issuer ----------------
-    if (lane == 0) {
-      constexpr uint32_t idesc = idesc_bf16<BN>();
-      int it = 0, lt = 0;
-      bool stop = false;
-      for (int t = blockIdx.x; t < T && !stop; t += gridDim.x, ++lt) {
-        const int b = lt & 1;
-        const uint32_t use = lt >> 1;
-        if (!mbar_wait(acc_empty(b), (use & 1) ^ 1u) || *(volatile int*)&s_flag[0]) {
-          stop = true;
-          break;
-        }
-        tc_fence_after();
-        const uint32_t dacc = tmem + b * BN;
-        for (int kb = 0; kb < KB; ++kb, ++it) {
-          const int s = it % STAGES;
-          const uint32_t ph = (it / STAGES) & 1;
-          if (!mbar_wait(full_bar(s), ph) || *(volatile int*)&s_flag[0]) {
-            stop = true;
-            break;
-          }
-          tc_fence_after();
-          if (lt == 0 && kb == 0) stamp(a, 2);
-#pragma unroll
-          for (int k = 0; k < BK / 16; ++k)
-            mma_bf16(dacc, sdesc_sw128(sA + s * Cfg::A_BYTES + k * 32), sdesc_sw128(sB + s * Cfg::B_BYTES + k * 32),
-                     idesc, (kb | k) != 0);
-          mma_commit(empty_bar(s));
-        }
-        if (lt == 0) stamp(a, 3);
-        mma_commit(acc_full(b));  // also after an abort: tracks every MMA issued into b
-        if (stop) {
-          (void)mbar_wait(acc_full(b), use & 1);  // those MMAs finish before the CTA frees TMEM
-          break;
-        }
-      }
-      if (stop) atomicOr(&s_flag[0], 1);
-    }
-  } else {
-    // ---------------- epilogue warps ----------------
-    constexpr int W = CPLX ? 2 : 1;
-    constexpr int RPT = BN / W;
-    constexpr int CW = (ModeTraits<MODE>::rk_mid || !CPLX) ? 8 : 16;
-    constexpr int NCH = (BN / 2) / CW;
-    const int e = threadIdx.x - 64;
-    const int q = warp & 3;
-    const int half = (warp - 2) >> 2;
-    const bool need_red = MODE == M_ENERGY || ((MODE == M_EULER || MODE == M_RK4) && a.rho_out != nullptr);
-    float* out = (MODE == M_ENERGY) ? a.e_part : ((MODE == M_EULER || MODE == M_RK4) ? a.rho_out : nullptr);
-    int bad = 0;
-    int lt = 0;
-    EpiRegs<MODE, CPLX, CW> R[2];
-    for (int t = blockIdx.x; t < T; t += gridDim.x, ++lt) {
-      const int mt = t / NT;
-      const int m0 = mt * BM, n0 = (t % NT) * BN;
-      const int b = lt & 1;
-      const uint32_t use = lt >> 1;
-      const int rbase = n0 / W;
-      const int i = m0 + 32 * q + lane;
-      const int cbeg = n0 + half * (BN / 2);
-      epi_load<MODE, CPLX, CW>(a, i, cbeg, R[0]);  // overlaps the MMAs
-      if (e < RPT) {
-        const int r = rbase + e;
-        const float bt = r < a.R ? a.beta_in[r] : 1.0f;
-        s_beta[e] = stage_beta(a, bt);
-        s_dsc[e] = r < a.R ? noise_scale(a, r) : 0.0f;
-      }
-      epi_bar_sync();
-      const bool ok = __all_sync(0xffffffffu, mbar_wait(acc_full(b), use & 1) && !*(volatile int*)&s_flag[0]);
-      tc_fence_after();
-      if (!ok) {
-        if (lane == 0) atomicOr(a.err, E_TIMEOUT);
-        atomicOr(&s_flag[0], 1);
-        break;
-      }
-      if (lt == 0 && e == 0) stamp(a, 4);
-      const uint32_t taddr = tmem + b * BN + (static_cast<uint32_t>(32 * q) << 16) + half * (BN / 2);
-      auto body = [&](int ch, const EpiRegs<MODE, CPLX, CW>& cur, EpiRegs<MODE, CPLX, CW>& nxt) {
-        if (ch + 1 < NCH) epi_load<MODE, CPLX, CW>(a, i, cbeg + (ch + 1) * CW, nxt);
-        float v[CW];
-        tmem_ld<CW>(taddr + ch * CW, v);
-        const int lr0 = (half * (BN / 2) + ch * CW) / W;
-        float red[CW / W];
-        epi_chunk<MODE, CPLX, CW>(a, i, cbeg + ch * CW, v, cur, &s_beta[lr0], &s_dsc[lr0], red, bad);
-        if (need_red) {
-#pragma unroll
-          for (int u = 0; u < CW / W; ++u) {
-            float x = red[u];
-#pragma unroll
-            for (int off = 16; off; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
-            if (lane == 0) s_red[q * BN + lr0 + u] = x;
-          }
-        }
-      };
-#pragma unroll 1
-      for (int ch = 0; ch + 1 < NCH; ch += 2) {
-        body(ch, R[0], R[1]);
-        body(ch + 1, R[1], R[0]);
-      }
-      if (NCH & 1) body(NCH - 1, R[0], R[1]);
-      tc_fence_before();
-      epi_bar_sync();
-      if (e == 0) mbar_arrive(acc_empty(b));  // accumulator b may be overwritten
-      if (lt == 0 && e == 0) stamp(a, 5);
-      if (e < RPT) {
-        const int r = rbase + e;
-        if (r < a.R) {
-          if (out)
-            out[size_t(mt) * a.Rp + r] = s_red[e] + s_red[BN + e] + s_red[2 * BN + e] + s_red[3 * BN + e];
-          if (mt == 0 && (MODE == M_EULER || MODE == M_RK4)) a.beta_out[r] = next_beta(a, a.beta_in[r]);
-        }
-      }
-    }
-    if (bad) s_flag[1] = 1;
-    epi_bar_sync();
-    if (e == 0 && s_flag[1]) atomicOr(a.err, E_DIVERGED);
-    if (e == 0) stamp(a, 6);
-  }
-
-  tc_fence_before();
-  __syncthreads();
-  if (threadIdx.x == 0 && s_flag[0]) atomicOr(a.err, E_TIMEOUT);
-  if (threadIdx.x == 0) stamp(a, 7);
-  if (warp == 1) {
-    tc_fence_after();
-    tmem_dealloc(tmem, TCOLS);
-  }
-}
-
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn get_encode() {
-  static EncodeTiledFn fn = nullptr;
-  if (!fn) {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-            cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeTiledFn>(p);
-  }
-  return fn;
-}
-
-// 2-D BF16 tensor [rows][Np] with a {64, box_rows} box and 128-byte swizzle.
-bool make_map(CUtensorMap* m, const void* ptr, int Np, int rows, int box_rows) {
-  EncodeTiledFn enc = get_encode();
-  if (!enc) return false;
-  const cuuint64_t dims[2] = {static_cast<cuuint64_t>(Np), static_cast<cuuint64_t>(rows)};
-  const cuuint64_t strides[1] = {static_cast<cuuint64_t>(Np) * 2};
-  const cuuint32_t box[2] = {static_cast<cuuint32_t>(BK), static_cast<cuuint32_t>(box_rows)};
-  const cuuint32_t es[2] = {1, 1};
-  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, es,
-             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
-template <int BN, int STAGES, bool CPLX, int MODE>
-cudaError_t launch_cfg(const CUtensorMap& A, const CUtensorMap& B, int b_row0, const StepArgs& a, cudaStream_t s) {
-  using Cfg = TcCfg<BN, STAGES>;
-  static bool attr_set = false;
-  auto kern = step_tc_kernel<BN, STAGES, CPLX, MODE>;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return cudaErrorUnknown;
-  }
-  const int tiles = ((a.C + BN - 1) / BN) * ((a.N + BM - 1) / BM);
-  kern<<<tiles < sms ? tiles : sms, NTHREADS, Cfg::SMEM, s>>>(A, B, b_row0, a);
-  return cudaGetLastError();
-}
-
-template <int BN, int STAGES, bool CPLX>
-cudaError_t dispatch_cplx(const CUtensorMap& A, const CUtensorMap& B, int b_row0, const StepArgs& a, cudaStream_t s) {
-  switch (a.mode) {
-    case M_EULER: return launch_cfg<BN, STAGES, CPLX, M_EULER>(A, B, b_row0, a, s);
-    case M_RK1: return launch_cfg<BN, STAGES, CPLX, M_RK1>(A, B, b_row0, a, s);
-    case M_RK2: return launch_cfg<BN, STAGES, CPLX, M_RK2>(A, B, b_row0, a, s);
-    case M_RK3: return launch_cfg<BN, STAGES, CPLX, M_RK3>(A, B, b_row0, a, s);
-    case M_RK4: return launch_cfg<BN, STAGES, CPLX, M_RK4>(A, B, b_row0, a, s);
-    case M_ENERGY: return launch_cfg<BN, STAGES, CPLX, M_ENERGY>(A, B, b_row0, a, s);
-    case M_RAW: return launch_cfg<BN, STAGES, CPLX, M_RAW>(A, B, b_row0, a, s);
-  }
-  return cudaErrorInvalidValue;
-}
-
-template <int BN, int STAGES>
-cudaError_t dispatch_mode(const CUtensorMap& A, const CUtensorMap& B, int b_row0, const StepArgs& a, cudaStream_t s) {
-  return a.cplx ? dispatch_cplx<BN, STAGES, true>(A, B, b_row0, a, s) : dispatch_cplx<BN, STAGES, false>(A, B, b_row0, a, s);
-}
-
-}  // namespace
-
-struct TcPlan {
-  CUtensorMap A;
-  CUtensorMap B128;
-  CUtensorMap B224;
-  CUtensorMap B256;
-  int Cp;
-};
 
 int tc_mtiles(int N) { return (N + BM - 1) / BM; }
 
@@ -374,9 +59,9 @@ const CUtensorMap* tc_plan_B(const TcPlan* plan) { return &plan->B128; }
 cudaError_t launch_step_tc(const TcPlan* plan, const StepArgs& a, int op_buf, cudaStream_t s) {
   const int b_row0 = op_buf * plan->Cp;
   const int bn = tc_pick_bn(a.N, a.C);
-  if (bn == 256) return dispatch_mode<256, 4>(plan->A, plan->B256, b_row0, a, s);
-  if (bn == 224) return dispatch_mode<224, 4>(plan->A, plan->B224, b_row0, a, s);
-  return dispatch_mode<128, 6>(plan->A, plan->B128, b_row0, a, s);
+  if (bn == 256) return dispatch_mode<256, 4, false>(plan->A, plan->B256, b_row0, a, s);
+  if (bn == 224) return dispatch_mode<224, 4, false>(plan->A, plan->B224, b_row0, a, s);
+  return dispatch_mode<128, 6, false>(plan->A, plan->B128, b_row0, a, s);
 }
 
 }  // namespace gda

@@ -7,6 +7,8 @@
 // paid about once per kernel instead of once per element.  The arithmetic is
 // the same FP32 expression sequence as epi_quad (epilogue.cuh).
 #pragma once
+#include <cuda_fp8.h>
+
 #include "epilogue.cuh"
 
 namespace gda {
@@ -162,6 +164,10 @@ __device__ __forceinline__ void epi_chunk(const StepArgs& a, int i, int c0, cons
           a.op_out[p0] = __float2bfloat16_rn(sr);
           if (CPLX) a.op_out[p0 + a.op_pitch] = __float2bfloat16_rn(si);
         }
+        if (a.op8_out) {
+          a.op8_out[o0] = __nv_cvt_float_to_fp8(sr * a.op8_inv, __NV_SATFINITE, __NV_E4M3);
+          if (CPLX) a.op8_out[o1] = __nv_cvt_float_to_fp8(si * a.op8_inv, __NV_SATFINITE, __NV_E4M3);
+        }
         continue;
       }
     }
@@ -176,6 +182,10 @@ __device__ __forceinline__ void epi_chunk(const StepArgs& a, int i, int c0, cons
       const size_t p0 = size_t(c0 + k0) * a.op_pitch + i;
       a.op_out[p0] = __float2bfloat16_rn(nr);
       if (CPLX) a.op_out[p0 + a.op_pitch] = __float2bfloat16_rn(ni);
+    }
+    if (a.op8_out) {
+      a.op8_out[o0] = __nv_cvt_float_to_fp8(nr * a.op8_inv, __NV_SATFINITE, __NV_E4M3);
+      if (CPLX) a.op8_out[o1] = __nv_cvt_float_to_fp8(ni * a.op8_inv, __NV_SATFINITE, __NV_E4M3);
     }
     const float rn = density(nr, ni);
     red[u] = rn;

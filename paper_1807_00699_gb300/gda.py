@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_HERE, "libgda.so")
 
 ISING, XY = 0, 1
 EULER, RK4 = 0, 1
-FP32, BF16 = 0, 1
+FP32, BF16, FP8 = 0, 1, 2
 AUTO, PER_STEP, RESIDENT = 0, 1, 2
 
 STATUS = {0: "GDA_OK", 1: "GDA_ERR_INVALID", 2: "GDA_ERR_CUDA", 3: "GDA_ERR_OOM", 4: "GDA_ERR_DIVERGED",

@@ -8,6 +8,7 @@ import numpy as np
 import pytest
 
 import synth
+import oracle
 from oracle import (Params, add_noise, energies, euler_step, field_drive,
                     hamiltonian_int, project, rhs, rk4_step, round_bf16, run)
 from oracle.gda_oracle import coupling_operand
@@ -204,3 +205,65 @@ def test_gda_finds_brute_force_ground_state_n20():
         S = project(psi)
         E = [hamiltonian_int(J, s) for s in S]
         assert min(E) == int(e_min)
+
+
+def test_round_e4m3_matches_torch():
+    torch = pytest.importorskip("torch")
+    if not hasattr(torch, "float8_e4m3fn"):
+        pytest.skip("no float8 in this torch")
+    x = np.concatenate([synth.normal(3, 20000) * 10.0 ** (2 * synth.normal(4, 20000)),
+                        [0.0, 448.0, 449.0, 1e6, -1e6, 2.0 ** -9, 1.5 * 2.0 ** -9, 0.5 * 2.0 ** -9, 240.0, 232.0]])
+    x = x.astype(np.float32)
+    ref = torch.tensor(np.clip(x, -448, 448)).to(torch.float8_e4m3fn).to(torch.float64).numpy()
+    assert np.array_equal(oracle.round_e4m3(x), ref)
+
+
+def test_e4m3_table_closed_form():
+    from oracle.gda_oracle import _E4M3
+    assert _E4M3[0] == 0 and _E4M3[1] == 2.0 ** -9 and _E4M3[8] == 2.0 ** -6
+    assert _E4M3[-1] == 448.0 and len(_E4M3) == 127 and np.all(np.diff(_E4M3) > 0)
+
+
+def test_fp8_coupling_exact_on_representable_operands():
+    # Row maxima 1 and 0.5 give scales 1/448 and 1/896; J0 / s and psi * 64
+    # then round to the E4M3 values 448 J0 / max and 64 psi, so the FP8
+    # product equals J0 psi up to the FP32 rounding of s.  A dropped row
+    # scale or amplitude scale fails here.
+    rng = np.random.default_rng(5)
+    n = 12
+    U = rng.choice([-1.0, -0.5, 0.5, 1.0, 0.0], size=(n, n))
+    J = np.triu(U, 1)
+    J = J + J.T
+    J[3] *= 0.5
+    J[:, 3] *= 0.5
+    J[3, 3] = 0.0
+    J[7, :] = 0.0  # an isolated spin: scale 1, zero row
+    J[:, 7] = 0.0
+    X = rng.choice([-0.75, -0.25, 0.0, 0.125, 0.5, 3.0], size=(4, n))
+    s = oracle.fp8_coupling_scales(J)
+    assert s[7] == 1.0 and s[3] == pytest.approx(np.abs(J[3]).max() / 448.0, rel=1e-7)
+    assert np.array_equal(oracle.round_e4m3(X * 64), X * 64)
+    mx = np.abs(J).max(1)
+    mx[7] = 448.0
+    assert np.array_equal(oracle.round_e4m3(J / s[:, None].astype(np.float32)), 448.0 * J / mx[:, None])
+    from oracle.gda_oracle import fp8_coupling
+    err = np.abs(fp8_coupling(J, X) - X @ J.T)
+    assert np.all(err <= 2.0 ** -23 * (np.abs(X) @ np.abs(J).T))
+
+
+def test_fp8_coupling_within_e4m3_rounding_bound():
+    # Each operand is rounded to 3 mantissa bits (relative error <= 2^-4 in
+    # the normal range), so |Y8 - Y| <= sum_j |J0_ij||X_j| (2^-3 + 2^-8),
+    # plus the subnormal floor of the amplitude operand.
+    from oracle.gda_oracle import fp8_coupling
+    n = 200
+    J, _ = synth.xy_gaussian(n, 3)
+    J0 = coupling_operand(J)
+    X = synth.initial_amplitudes(n, 6, 4, 1.0, False)
+    Y8, Y = fp8_coupling(J0, X), X @ J0.T
+    bound = (np.abs(X) @ np.abs(J0).T) * (2.0 ** -3 + 2.0 ** -8) + np.abs(J0).sum(1)[None, :] * 2.0 ** -16
+    assert np.all(np.abs(Y8 - Y) <= bound)
+    assert np.abs(Y8 - Y).max() > 1e-4 * np.abs(Y).max()  # the rounding is really applied
+    # saturation: amplitudes beyond 448 / 64 = 7 are clipped
+    X2 = np.full((1, n), 10.0)
+    assert np.allclose(fp8_coupling(J0, X2), fp8_coupling(J0, np.full((1, n), 7.0)))
