@@ -38,11 +38,22 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="bf16", choices=["bf16", "fp32"])
+    ap.add_argument("--prec", default="bf16", choices=["bf16", "fp32", "fp8"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32-ttt", action="store_true")
-    ap.add_argument("--workload", default="xy1000", choices=["xy1000", "batched"],
-                    help="xy1000: the headline workload; batched: the 2000-instance serving mix")
+    ap.add_argument("--workload", default="xy1000", choices=["xy1000", "batched", "sk4096", "kernel"],
+                    help="xy1000: the headline workload; batched: the 2000-instance serving mix; "
+                         "sk4096: SK N=4096 R=4096 quality per precision (FP32 / BF16 / FP8); "
+                         "kernel: time per step of one configuration (the small cases profiled with ncu)")
+    ap.add_argument("--model", default="xy", choices=["xy", "ising"], help="kernel workload: XY (J ~ N(0, 1/N)) "
+                    "or Ising SK (J ~ N(0, 1))")
+    ap.add_argument("--n", type=int, default=1000, help="kernel workload: spins")
+    ap.add_argument("--r", type=int, default=1024, help="kernel workload: restarts")
+    ap.add_argument("--sched", default="auto", choices=["auto", "per_step", "resident"])
+    ap.add_argument("--integ", default="euler", choices=["euler", "rk4"])
+    ap.add_argument("--kernel-steps", type=int, default=20, help="kernel workload: timed steps")
+    ap.add_argument("--timeline", action="store_true", help="kernel workload: per-CTA device timestamps")
+    ap.add_argument("--sk-seeds", default="0", help="comma-separated instance seeds of the sk4096 workload")
     ap.add_argument("--batch-count", type=int, default=2000)
     return ap.parse_args()
 
@@ -167,7 +178,7 @@ def run_ours(args):
 
     W = WORKLOAD
     J, g = instance()
-    prec = gda.BF16 if args.prec == "bf16" else gda.FP32
+    prec = {"fp32": gda.FP32, "bf16": gda.BF16, "fp8": gda.FP8}[args.prec]
     stream = torch.cuda.Stream()
     s = gda.Solver(J, g, gda.XY, stream=stream)
     seed = W["seed"] + 1000 * rank  # ranks run independent restart sets (weak scaling)
@@ -239,14 +250,19 @@ def run_ours(args):
     if prec == gda.BF16:
         peak = peaks.get("bf16_tflops", 1900.0)
         src = "measured bf16 burst" if "bf16_tflops" in peaks else "fallback"
+    elif prec == gda.FP8:
+        peak = 2.0 * peaks.get("bf16_tflops", 1900.0)
+        src = ("measured bf16 burst x 2 (nominal fp8 / bf16 ratio)" if "bf16_tflops" in peaks
+               else "fallback x 2")
     else:
         peak = 152 * 128 * 2 * 2.07e9 / 1e12
         src = "nominal FP32 CUDA-core rate (152 SMs x 128 FMA x 2.07 GHz)"
     achieved = flops / t_kernel / 1e12
-    roofline = {"bound": "tensor" if prec == gda.BF16 else "alu", "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                "kernel": ("step_res_kernel (resident: GEMM + fused epilogue, state in TMEM), time per step"
-                           if prec == gda.BF16 else "step_simt_kernel"),
+    kname = {gda.BF16: "step_res_kernel (resident: GEMM + fused epilogue, state in TMEM), time per step",
+             gda.FP8: "step_tc_kernel (per-step, E4M3 operands), time per step",
+             gda.FP32: "step_simt_kernel"}[prec]
+    roofline = {"bound": "alu" if prec == gda.FP32 else "tensor", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None, "kernel": kname,
                 "peak_source": src, "us_per_launch": t_kernel * 1e6}
 
     # end to end through host buffers: load J, solve, read the best configuration back
@@ -322,7 +338,7 @@ def run_ours(args):
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "spin-updates/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "bf16" if prec == gda.BF16 else "f32", "data": "synthetic",
+                "vs_baseline": None, "dtype": {gda.BF16: "bf16", gda.FP8: "fp8_e4m3", gda.FP32: "f32"}[prec], "data": "synthetic",
                 "config": {"workload": W["name"], "model": "xy", "N": W["N"], "R": W["R"], "steps": W["steps"],
                            "integrator": "euler", "dt": W["dt"], "energy_every": W["energy_every"],
                            "l2": "flushed (256 MB write) between timed steps", "parallelism": f"replicas{world}"},
@@ -421,12 +437,149 @@ def run_batched(args):
     b.close()
 
 
+SK = dict(N=4096, R=4096, steps=10000, dt_sqrtN=0.1, eps=0.03, beta0=0.5, eps_hat=0.05, rho_th=1.0,
+          init_amp=1e-3, energy_every=100)
+
+
+def run_sk(args):
+    """SK instances, J_ij ~ N(0, 1) symmetric, zero diagonal, g = 0, N = 4096,
+    R = 4096 restarts, 10000 forward-Euler steps with the coupling ramp
+    (beta0 = 0.5, eps_hat = 0.05), dt = 0.1 / sqrt(N), eps = 0.03, through the
+    FP32, BF16 and FP8 coupling products on the same seeded start.  Per
+    precision: solve time, spin-updates/s, coupling TFLOP/s, the best FP64
+    energy, its gap to the best FP64-verified energy of all three, and the
+    success probability (share of restarts within 1e-3 relative of it)."""
+    import torch
+
+    import __graft_entry__
+    import synth
+    torch.cuda.set_device(0)
+    __graft_entry__.build()
+    from paper_1807_00699_gb300 import gda
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    bf16_peak = peaks.get("bf16_tflops_sustained", 1700.0)
+    N, R, steps = SK["N"], SK["R"], SK["steps"]
+    dt = SK["dt_sqrtN"] / math.sqrt(N)
+    precs = [("fp32", gda.FP32), ("bf16", gda.BF16), ("fp8", gda.FP8)]
+    stream = torch.cuda.Stream()
+    rows = []
+    with ClockSampler(0) as clocks:
+        for seed in [int(x) for x in args.sk_seeds.split(",")]:
+            J, _ = synth.sk_gaussian(N, seed)
+            res = {}
+            for name, prec in precs:
+                s = gda.Solver(J, None, gda.ISING, stream=stream)
+                kw = dict(dt=dt, eps=SK["eps"], beta0=SK["beta0"], eps_hat=SK["eps_hat"], rho_th=SK["rho_th"],
+                          init_amp=SK["init_amp"], seed=100 + seed, prec=prec, schedule=gda.PER_STEP)
+                s.run(gda.default_params(init_mode=1, **kw), R, 20)  # warm-up
+                s.sync()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                s.run(gda.default_params(init_mode=1, energy_every=SK["energy_every"], **kw), R, steps)
+                E = s.energy()
+                e1.record(stream)
+                e1.synchronize()
+                t = e0.elapsed_time(e1) / 1e3
+                st, Et, _ = s.trace()
+                res[name] = (E, t, st, Et)
+                s.close()
+            Estar = min(float(r[0].min()) for r in res.values())
+            target = Estar + 1e-3 * abs(Estar)
+            for name, (E, t, st, Et) in res.items():
+                hit = np.nonzero(Et <= target)[0]
+                flops = 2.0 * N * N * R * steps / t / 1e12
+                peak = bf16_peak * (2.0 if name == "fp8" else 1.0) if name != "fp32" else None
+                rows.append({"seed": seed, "prec": name, "solve_s": t, "spin_updates_per_s": N * R * steps / t,
+                             "tflops": flops, "frac_of_sustained_peak": (flops / peak) if peak else None,
+                             "E_best_fp64": float(E.min()), "E_star_fp64": Estar,
+                             "gap_rel": (float(E.min()) - Estar) / abs(Estar),
+                             "success_prob": float(np.mean(E <= target)),
+                             "E_median_fp64": float(np.median(E)),
+                             "ttt_s": None if len(hit) == 0 else float(st[hit[0]]) / steps * t})
+    bf = [r for r in rows if r["prec"] == "bf16"]
+    line = {"metric": "energy gap & success probability per precision; spin-updates/s",
+            "value": float(np.mean([r["spin_updates_per_s"] for r in bf])), "unit": "spin-updates/s",
+            "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": float(np.mean([r["solve_s"] for r in bf])) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": "sk_gaussian_N4096_R4096_10000steps_ramp", **SK, "dt": dt,
+                       "seeds": args.sk_seeds, "schedule": "per-step",
+                       "peak": f"bf16 sustained {bf16_peak} TFLOP/s (measured); fp8 = 2x (nominal ratio)"},
+            "per_precision": rows, "clocks": clocks.summary()}
+    print(json.dumps(line), flush=True)
+
+
+def run_kernel(args):
+    """Time per step of one configuration: 3 untimed steps, then
+    --kernel-steps steps in one gda_run on a side stream (CUDA events).
+    Ising instances are SK (J ~ N(0, 1), dt = 0.1 / sqrt(N)), XY instances
+    J ~ N(0, 1/N) (dt = 0.05).  With --timeline, the per-CTA device
+    timestamps of the last launch (entry, setup done, first MMA issued, last
+    MMA issued, first accumulator ready, first epilogue done, partials
+    written, exit) as min / median / max microseconds from the first entry."""
+    import torch
+
+    import __graft_entry__
+    import synth
+    torch.cuda.set_device(0)
+    __graft_entry__.build()
+    from paper_1807_00699_gb300 import gda
+    N, R = args.n, args.r
+    if args.model == "xy":
+        J, g = synth.xy_gaussian(N, 1)
+        dt = 0.05
+    else:
+        J, g = synth.sk_gaussian(N, 1)
+        dt = 0.1 / math.sqrt(N)
+    prec = {"fp32": gda.FP32, "bf16": gda.BF16, "fp8": gda.FP8}[args.prec]
+    sched = {"auto": gda.AUTO, "per_step": gda.PER_STEP, "resident": gda.RESIDENT}[args.sched]
+    integ = gda.RK4 if args.integ == "rk4" else gda.EULER
+    stream = torch.cuda.Stream()
+    s = gda.Solver(J, g, gda.XY if args.model == "xy" else gda.ISING, stream=stream)
+    kw = dict(dt=dt, eps=0.1, prec=prec, schedule=sched, integ=integ)
+    s.run(gda.default_params(init_mode=1, seed=1, **kw), R, 3)
+    s.sync()
+    if args.timeline:
+        s.profile(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.run(gda.default_params(init_mode=2, **kw), R, args.kernel_steps)
+    e1.record(stream)
+    s.sync()
+    t = e0.elapsed_time(e1) / 1e3 / args.kernel_steps
+    C = R * (2 if args.model == "xy" else 1)
+    flops = 2.0 * N * N * C * (4 if integ == gda.RK4 else 1)
+    line = {"workload": "kernel", "model": args.model, "N": N, "R": R, "prec": args.prec, "sched": args.sched,
+            "integ": args.integ, "steps": args.kernel_steps, "us_per_step": t * 1e6,
+            "tflops": flops / t / 1e12, "spin_updates_per_s": N * R / t}
+    if args.timeline:
+        st = s.profile_read()
+        ctas = st[st[:, 0] > 0]
+        rel = (ctas.astype(np.int64) - int(ctas[:, 0].min())) / 1e3
+        names = ["entry", "setup", "tile0", "lastmma", "accready", "epidone", "partials", "exit"]
+        line["timeline_us"] = {nm: [float(rel[:, k].min()), float(np.median(rel[:, k])), float(rel[:, k].max())]
+                               for k, nm in enumerate(names)}
+        line["ctas"] = int(len(ctas))
+        s.profile(False)
+    print(json.dumps(line), flush=True)
+    s.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batched":
         run_batched(args)
+    elif args.workload == "sk4096":
+        run_sk(args)
+    elif args.workload == "kernel":
+        run_kernel(args)
     else:
         run_ours(args)
 
