@@ -17,7 +17,12 @@ gain-dissipative systems" (2018):
            with Delta_ij = 1 and K(0) = beta0 J, so K(t) = beta(t) J with
            d beta/dt = eps_hat (1 - beta) (a per-restart coupling ramp);
 * Sec. 2   fourth-order Runge-Kutta time stepping (forward Euler also given);
-* Sec. 2-3 many restarts per instance, best energy kept.
+* Sec. 2-3 many restarts per instance, best energy kept;
+* Sec. 2   the GD-mod algorithm: Eq. (6) with Delta_ij = gamma_i^inj +
+           gamma_j^inj and a full coupling matrix K per restart (forward
+           Euler; gamma^inj = gamma + gamma_c with gamma_c a parameter);
+* FP8 / BF16 rounding of the coupling operands (not in the paper): the
+           rounding rules the tensor-core path applies, for parity only.
 
 Notation: gamma is the effective gain gamma^inj - gamma_c (only the difference
 enters Eq. 2).  psi has shape (R, N): R independent restarts of N spins.
@@ -41,9 +46,11 @@ Readings of points the paper leaves open (all listed in the design notes):
 
 Every function below is pinned by `tests/test_oracle_*.py` against closed
 forms, invariants, brute force or library routines (see each docstring).
-Parity unpinned: none of the functions here; the BF16 operand-rounding variant
-of the step is pinned only through its rounding rule (test against torch's
-bfloat16 conversion) and the FP64 step it wraps.
+Parity unpinned: none of the functions here; the BF16 and FP8 operand-rounding
+variants of the step are pinned through their rounding rules (tests against
+torch's bfloat16 and float8_e4m3fn conversions, the E4M3 table's closed form,
+an exactly representable instance and the E4M3 error bound) and the FP64 step
+they wrap.
 """
 from __future__ import annotations
 
@@ -58,6 +65,7 @@ __all__ = [
     "philox_generic", "philox_uniform", "box_muller", "noise_xi",
     "init_amplitudes", "rhs", "euler_step", "rk4_step", "add_noise",
     "run", "round_bf16", "best_of", "field_drive", "round_e4m3", "fp8_coupling_scales",
+    "gdmod_rhs", "gdmod_euler_step", "gdmod_run",
 ]
 
 # --------------------------------------------------------------------------
@@ -86,6 +94,7 @@ class Params:
     init_amp: float = 1e-3
     energy_every: int = 0         # record best energy every k steps (0: off)
     operand: str = "fp64"         # 'fp64', 'bf16' or 'fp8' rounding of the J.Psi operands
+    gamma_c: float = 1.0          # loss rate: gamma^inj = gamma + gamma_c (GD-mod's Delta only)
 
     def with_(self, **kw) -> "Params":
         return replace(self, **kw)
@@ -454,3 +463,72 @@ def run(J, g, model: str, p: Params, R: int, steps: int, state=None, step0: int 
             E = energies(J, g, project(psi))
             trace.append((n + 1,) + best_of(E))
     return psi, gamma, beta
+
+
+# --------------------------------------------------------------------------
+# GD-mod: coupling feedback with injection-dependent coupling (Eq. 6 with
+# Delta_ij = gamma_i^inj + gamma_j^inj) and a per-restart coupling matrix K.
+# --------------------------------------------------------------------------
+
+def gdmod_rhs(psi, gamma, K, J0, h1, p: Params):
+    """Time derivatives (f, u, w) of (psi, gamma, K) in the GD-mod algorithm.
+
+    gamma^inj_i = gamma_i + gamma_c (the state carries gamma^inj - gamma_c),
+    Delta_ij = gamma^inj_i + gamma^inj_j (Sec. 2, geometrically coupled case),
+    f_i  = psi_i (gamma_i - |psi_i|^2) + sum_{j != i} Delta_ij K_ij psi_j + h_1i  (Eq. 2)
+    u_i  = eps (rho_th - |psi_i|^2)                                            (Eq. 5)
+    w_ij = eps_hat (J_ij - Delta_ij K_ij)                                      (Eq. 6)
+    psi, gamma: (R, N); K: (R, N, N) with a zero diagonal (K_ii stays 0
+    because J0_ii = 0 and K_ii(0) = 0)."""
+    rho = np.real(psi * np.conj(psi))
+    ginj = gamma + p.gamma_c
+    Delta = ginj[:, :, None] + ginj[:, None, :]
+    DK = Delta * K
+    Y = np.einsum("rij,rj->ri", DK, psi)
+    f = psi * (gamma - rho) + Y + h1[None, :]
+    u = p.eps * (p.rho_th - rho)
+    w = p.eps_hat * (J0[None, :, :] - DK)
+    return f, u, w
+
+
+def gdmod_euler_step(state, J0, h1, p: Params):
+    """Forward Euler over (psi, gamma, K), all derivatives at time t."""
+    psi, gamma, K = state
+    f, u, w = gdmod_rhs(psi, gamma, K, J0, h1, p)
+    return psi + p.dt * f, gamma + p.dt * u, K + p.dt * w
+
+
+def gdmod_run(J, g, model: str, p: Params, R: int, steps: int, state=None, step0: int = 0,
+              trace: list | None = None):
+    """Evolve R restarts for `steps` forward-Euler steps of the GD-mod
+    algorithm (Eqs. 2, 5, 6 with Delta_ij = gamma_i^inj + gamma_j^inj).
+    Initial state: psi by p.init_mode as in run(), gamma = gamma0,
+    K = beta0 J0 for every restart.  Noise as in run().  Returns the final
+    (psi, gamma, K); `trace` as in run()."""
+    if p.integ != "euler":
+        raise ValueError("GD-mod is integrated with forward Euler")
+    J = np.asarray(J, dtype=np.float64)
+    N = J.shape[0]
+    g = np.zeros(N) if g is None else np.asarray(g, dtype=np.float64)
+    complex_ = model == "xy"
+    J0 = coupling_operand(J)
+    h1 = field_drive(g, p.rho_th)
+    if state is None:
+        if p.init_mode == 1:
+            psi = init_amplitudes(p.seed, R, N, p.init_amp, complex_)
+        else:
+            psi = np.zeros((R, N), dtype=np.complex128 if complex_ else np.float64)
+        gamma = np.full((R, N), float(p.gamma0))
+        K = np.broadcast_to(float(p.beta0) * J0, (R, N, N)).copy()
+    else:
+        psi, gamma, K = (np.array(x, copy=True) for x in state)
+        if complex_:
+            psi = psi.astype(np.complex128)
+    for n in range(step0, step0 + steps):
+        new = gdmod_euler_step((psi, gamma, K), J0, h1, p)
+        psi_new = add_noise(new[0], psi, n, p, complex_)
+        psi, gamma, K = psi_new, new[1], new[2]
+        if p.energy_every and trace is not None and (n + 1 - step0) % p.energy_every == 0:
+            E = energies(J, g, project(psi))
+            trace.append((n + 1,) + best_of(E))
+    return psi, gamma, K
