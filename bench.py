@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--r", type=int, default=1024, help="kernel workload: restarts")
     ap.add_argument("--sched", default="auto", choices=["auto", "per_step", "resident"])
     ap.add_argument("--integ", default="euler", choices=["euler", "rk4"])
+    ap.add_argument("--coupling", default="gd", choices=["gd", "gdmod"],
+                    help="kernel workload: GD (K = beta J) or GD-mod (per-restart K, FP32)")
     ap.add_argument("--kernel-steps", type=int, default=20, help="kernel workload: timed steps")
     ap.add_argument("--timeline", action="store_true", help="kernel workload: per-CTA device timestamps")
     ap.add_argument("--sk-seeds", default="0", help="comma-separated instance seeds of the sk4096 workload")
@@ -541,6 +543,11 @@ def run_kernel(args):
     stream = torch.cuda.Stream()
     s = gda.Solver(J, g, gda.XY if args.model == "xy" else gda.ISING, stream=stream)
     kw = dict(dt=dt, eps=0.1, prec=prec, schedule=sched, integ=integ)
+    gdmod = args.coupling == "gdmod"
+    if gdmod:  # gamma_c above the coupling scale keeps Delta > 0 (2 for XY, 2 sqrt(N) for SK);
+        # Delta(0) K(0) = 2 gamma_c beta0 J = 0.6 J
+        gc = 3.0 if args.model == "xy" else 3.0 * math.sqrt(N)
+        kw.update(coupling=gda.GDMOD, eps_hat=0.5, beta0=0.3 / gc, gamma_c=gc)
     s.run(gda.default_params(init_mode=1, seed=1, **kw), R, 3)
     s.sync()
     if args.timeline:
@@ -555,8 +562,13 @@ def run_kernel(args):
     C = R * (2 if args.model == "xy" else 1)
     flops = 2.0 * N * N * C * (4 if integ == gda.RK4 else 1)
     line = {"workload": "kernel", "model": args.model, "N": N, "R": R, "prec": args.prec, "sched": args.sched,
-            "integ": args.integ, "steps": args.kernel_steps, "us_per_step": t * 1e6,
+            "integ": args.integ, "coupling": args.coupling, "steps": args.kernel_steps, "us_per_step": t * 1e6,
             "tflops": flops / t / 1e12, "spin_updates_per_s": N * R / t}
+    if gdmod:  # K read and written once per step: 8 bytes per element of R x N x Np
+        Np = (N + 127) // 128 * 128
+        line["tflops"] = None
+        line["k_bytes_per_step"] = 8 * R * N * Np
+        line["gbs"] = 8 * R * N * Np / t / 1e9
     if args.timeline:
         st = s.profile_read()
         ctas = st[st[:, 0] > 0]

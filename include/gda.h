@@ -92,7 +92,24 @@ typedef struct {
                            3: as 1 plus the per-spin base of gda_set_init_base */
   int32_t schedule;     /* gda_schedule: how BF16 steps are launched           */
   double init_amp;      /* a for init_mode 1                                   */
+  int32_t coupling;     /* gda_coupling_mode: GD (K = beta J) or GD-mod        */
+  int32_t reserved;     /* 0                                                   */
+  double gamma_c;       /* GD-mod: loss rate, gamma^inj = gamma + gamma_c      */
 } gda_params;
+
+/* Coupling feedback of Eq. (6).
+ * GDA_COUPLING_GD: Delta_ij = 1 and K(0) = beta0 J, so K(t) = beta(t) J with
+ *   d beta/dt = eps_hat (1 - beta) per restart: one GEMM per step.
+ * GDA_COUPLING_GDMOD (Sec. 2, the GD-mod algorithm): Delta_ij = gamma_i^inj +
+ *   gamma_j^inj with gamma^inj = gamma + gamma_c, and a full coupling matrix
+ *   K_r per restart, K_r(0) = beta0 J, dK_ij/dt = eps_hat (J_ij - Delta_ij
+ *   K_ij); the coupling sum is sum_{j != i} Delta_ij K_ij psi_j.  K takes
+ *   R * N * Np * 4 bytes of device memory (Np = N rounded up to 128) and is
+ *   streamed from HBM every step.  Requires GDA_FP32, GDA_EULER, no noise
+ *   decay, Np * 12 bytes <= 227 KB; else GDA_ERR_UNSUPPORTED.  K lives in the
+ *   context: init_mode 2 continues it, gda_set_state does not touch it, and
+ *   gda_get_state does not return it. */
+typedef enum { GDA_COUPLING_GD = 0, GDA_COUPLING_GDMOD = 1 } gda_coupling_mode;
 
 /* Launch schedule of the tensor-core path.  AUTO picks the resident kernel
  * for Euler runs whose 128 x 128 tiles all fit on the device at once (every
@@ -106,7 +123,8 @@ typedef enum {
 } gda_schedule;
 
 /* Fills p with dt = 0.01, eps = 0.1, rho_th = 1, gamma0 = 0, beta0 = 1,
- * eps_hat = 0, noise off, Euler, FP32, init_mode 1 with a = 1e-3, seed 0. */
+ * eps_hat = 0, noise off, Euler, FP32, init_mode 1 with a = 1e-3, seed 0,
+ * GDA_COUPLING_GD, gamma_c = 1. */
 void gda_default_params(gda_params* p);
 
 /* Creates a context for an N-spin instance on the current CUDA device.

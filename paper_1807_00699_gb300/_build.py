@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgda.so")
-SOURCES = ["gda_api.cu", "step_simt.cu", "step_tc.cu", "step_tc8.cu", "energy.cu", "noalloc.cu", "step_res.cu", "mlp.cu", "step_batch.cu"]
+SOURCES = ["gda_api.cu", "step_simt.cu", "step_tc.cu", "step_tc8.cu", "gdmod.cu", "energy.cu", "noalloc.cu", "step_res.cu", "mlp.cu", "step_batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

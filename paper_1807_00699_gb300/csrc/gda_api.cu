@@ -62,6 +62,9 @@ struct gda_ctx {
   __nv_bfloat16* ops = nullptr;  // [3][Cp][Np]: operand ping-pong + projected spins
   unsigned char* ops8 = nullptr;  // [2][Cp][Np]: E4M3 operand ping-pong (FP8 path)
   TcPlan* plan8 = nullptr;
+  float* K = nullptr;  // GD-mod per-restart couplings [K_R][N][Np]
+  size_t K_cap = 0;
+  int K_R = 0;         // restarts K was initialised for (0: none)
   double* S64 = nullptr;
   int* Sint = nullptr;
   double* part64 = nullptr;
@@ -212,6 +215,7 @@ gda_status load_instance(gda_ctx* c, const double* J, const double* g, cudaMemcp
   CK(cudaMemcpy2DAsync(c->J64, Np * sizeof(double), J, N * sizeof(double), N * sizeof(double), N, kind, c->stream));
   CK(cudaMemsetAsync(c->g64, 0, Np * sizeof(double), c->stream));
   if (g) CK(cudaMemcpyAsync(c->g64, g, N * sizeof(double), kind, c->stream));
+  c->K_R = 0;  // a GD-mod coupling state belongs to the previous J
   CK(cudaMemsetAsync(c->d_flags, 0, sizeof(int), c->stream));
   CK(cudaMemsetAsync(c->d_maxabs, 0, sizeof(unsigned long long), c->stream));
   LK(launch_check_instance(c->J64, c->g64, c->N, c->Np, c->d_flags, c->d_maxabs, c->d_diag, c->stream));
@@ -280,6 +284,15 @@ gda_status check_params(gda_ctx* c, const gda_params* p) {
     return fail(c, GDA_ERR_INVALID, "unknown schedule %d", p->schedule);
   if (p->prec != GDA_FP32 && !c->tc_ok)
     return fail(c, GDA_ERR_UNSUPPORTED, "tensor-core path needs an sm_103 device");
+  if (p->coupling != GDA_COUPLING_GD && p->coupling != GDA_COUPLING_GDMOD)
+    return fail(c, GDA_ERR_INVALID, "unknown coupling mode %d", p->coupling);
+  if (p->coupling == GDA_COUPLING_GDMOD) {
+    if (!finite(p->gamma_c)) return fail(c, GDA_ERR_INVALID, "non-finite gamma_c");
+    if (p->prec != GDA_FP32 || p->integ != GDA_EULER || p->schedule == GDA_SCHEDULE_RESIDENT)
+      return fail(c, GDA_ERR_UNSUPPORTED, "GD-mod runs FP32 forward Euler, per step");
+    if (p->noise_D != 0.0 && p->noise_decay) return fail(c, GDA_ERR_UNSUPPORTED, "GD-mod has no noise decay");
+    if (gdmod_smem_bytes(c->Np, c->cplx) > 227 * 1024) return fail(c, GDA_ERR_UNSUPPORTED, "N too large for GD-mod");
+  }
   return GDA_OK;
 }
 
@@ -333,6 +346,44 @@ gda_status track(gda_ctx* c, const gda_params* p, bool tc, long long step) {
   return GDA_OK;
 }
 
+// GD-mod (Sec. 2): one K-streaming launch per step, FP32, forward Euler.
+gda_status run_gdmod(gda_ctx* c, const gda_params* p, int R, int64_t steps) {
+  const size_t need = size_t(R) * c->N * c->Np;
+  const long long nrb = (c->N + 31) / 32;
+  if (nrb * R >= (1LL << 31)) return fail(c, GDA_ERR_UNSUPPORTED, "too many GD-mod row blocks");
+  if (p->init_mode == 2) {
+    if (!c->K || c->K_R != R) return fail(c, GDA_ERR_STATE, "GD-mod continuation needs a GD-mod state with the same R");
+  } else {
+    if (c->K_cap < need) {
+      dfree(c->K);
+      c->K_cap = 0;
+      CK(dalloc(&c->K, need));
+      c->K_cap = need;
+    }
+    LK(launch_gdmod_init(c->K, c->J32, float(p->beta0), c->N, c->Np, R, c->stream));
+    c->K_R = R;
+  }
+  const StepArgs base = base_args(c, p, false);
+  const float ceh = float(p->dt * p->eps_hat);
+  for (int64_t k = 0; k < steps; ++k) {
+    const long long n = c->step + k;
+    StepArgs a = base;
+    a.step = static_cast<unsigned int>(n);
+    a.psi_n = c->psi[c->cur];
+    a.psi_out = c->psi[c->cur ^ 1];
+    a.beta_in = c->beta[c->bcur];
+    LK(launch_gdmod_step(a, c->J32, c->K, c->gam, c->gstg, float(p->gamma_c), ceh, c->stream));
+    std::swap(c->gam, c->gstg);
+    c->cur ^= 1;
+    if (p->energy_every > 0 && (k + 1) % p->energy_every == 0) {
+      gda_status s = track(c, p, false, n + 1);
+      if (s != GDA_OK) return s;
+    }
+  }
+  c->step += steps;
+  return GDA_OK;
+}
+
 gda_status compute_energies(gda_ctx* c) {
   if (!c->have_state) return fail(c, GDA_ERR_STATE, "no state: call gda_run or gda_set_state first");
   if (c->int_exact) {
@@ -379,6 +430,8 @@ void gda_default_params(gda_params* p) {
   p->seed = 0;
   p->init_mode = 1;
   p->init_amp = 1e-3;
+  p->coupling = GDA_COUPLING_GD;
+  p->gamma_c = 1.0;
 }
 
 const char* gda_status_string(gda_status s) {
@@ -407,6 +460,7 @@ void gda_destroy(gda_ctx* c) {
   dfree(c->bestE); dfree(c->bestR); dfree(c->cfg8); dfree(c->cfgth);
   dfree(c->t_step); dfree(c->t_E); dfree(c->t_r); dfree(c->t_count); dfree(c->err); dfree(c->flags);
   dfree(c->stamps);
+  dfree(c->K);
   dfree(c->fw[0]);
   dfree(c->fw[1]);
   dfree(c->base);
@@ -528,6 +582,7 @@ gda_status gda_run(gda_ctx* c, const gda_params* p, int32_t R, int64_t steps) {
   LK(launch_fill_h1(c->g64, c->h1, c->N, float(std::sqrt(p->rho_th)), c->stream));
   // field in FP32 for the tracking energy
   LK(launch_fill_h1(c->g64, c->g32, c->N, -1.0f, c->stream));
+  if (p->coupling == GDA_COUPLING_GDMOD) return run_gdmod(c, p, R, steps);
   const size_t cn = size_t(c->Cp) * c->Np;
   c->opcur = 0;
   if (f8) {

@@ -96,6 +96,13 @@ cudaError_t launch_step_tc8(const TcPlan* plan, const StepArgs& a, int op_buf, c
 constexpr float kFp8PsiScale = 1.0f / 64.0f;
 // J8_ij = e4m3(J32_ij / s_i), s_i = max_j |J32_ij| / 448 (1 for a zero row).
 cudaError_t launch_prepare_J8(const float* J32, int Np, unsigned char* J8, float* scale, cudaStream_t s);
+// GD-mod (Eq. 6 with Delta_ij = gamma_i^inj + gamma_j^inj): K[r][i][j] =
+// beta0 J[i][j] for R restarts; one forward-Euler step reading gin, writing
+// gout and updating K in place.
+size_t gdmod_smem_bytes(int Np, bool cplx);
+cudaError_t launch_gdmod_init(float* K, const float* J, float beta0, int N, int Np, int R, cudaStream_t s);
+cudaError_t launch_gdmod_step(const StepArgs& a, const float* J, float* K, const float* gin, float* gout,
+                              float gamma_c, float ceh, cudaStream_t s);
 // y = e4m3(x / kFp8PsiScale), n elements.
 cudaError_t launch_to_e4m3(const float* x, unsigned char* y, size_t n, cudaStream_t s);
 int tc_mtiles(int N);

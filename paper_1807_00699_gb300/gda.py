@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libgda.so")
 ISING, XY = 0, 1
 EULER, RK4 = 0, 1
 FP32, BF16, FP8 = 0, 1, 2
+GD, GDMOD = 0, 1  # coupling feedback (gda_coupling_mode)
 AUTO, PER_STEP, RESIDENT = 0, 1, 2
 
 STATUS = {0: "GDA_OK", 1: "GDA_ERR_INVALID", 2: "GDA_ERR_CUDA", 3: "GDA_ERR_OOM", 4: "GDA_ERR_DIVERGED",
@@ -34,7 +35,8 @@ class Params(ct.Structure):
                 ("rho_th", ct.c_double), ("gamma0", ct.c_double), ("beta0", ct.c_double),
                 ("eps_hat", ct.c_double), ("noise_D", ct.c_double), ("noise_decay", ct.c_int32),
                 ("energy_every", ct.c_int32), ("seed", ct.c_uint64), ("init_mode", ct.c_int32),
-                ("schedule", ct.c_int32), ("init_amp", ct.c_double)]
+                ("schedule", ct.c_int32), ("init_amp", ct.c_double), ("coupling", ct.c_int32),
+                ("reserved", ct.c_int32), ("gamma_c", ct.c_double)]
 
 
 SIGNATURES = {
