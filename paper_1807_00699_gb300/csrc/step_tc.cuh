@@ -7,8 +7,9 @@
 // One CTA computes one 128 x BN tile of Y (spins x columns).  Warp roles:
 //   warp 0        TMA producer (one elected lane), STAGES-deep ring
 //   warp 1        TMEM allocator and MMA issuer (one elected lane)
-//   warps 2..9    epilogue: warp w reads TMEM lane quarter (w % 4), half of
-//                 the columns each, and runs the per-element update.
+//   warps 2..      epilogue (16 warps, 8 for RK stages 2-4): warp w reads
+//                 TMEM lane quarter (w % 4) and one of 4 (2) column parts,
+//                 and runs the per-element update.
 // A pipeline stage holds 128 bytes of K per row in either precision (64 BF16
 // or 128 E4M3 values), so stage sizes, swizzle and descriptors are shared.
 // Every mbarrier wait is bounded by a clock budget; on expiry the CTA records
@@ -26,7 +27,15 @@ namespace gda {
 namespace {
 
 using namespace ptx;
-constexpr int NTHREADS = 320;
+// Epilogue warps per CTA: 16 for Euler, RK stage 1, energy and raw launches;
+// 8 for RK stages 2-4, whose extra stage registers need the larger per-thread
+// budget of a 320-thread block.  The epilogue streams the FP32 state, and
+// twice the warps keep twice the loads and stores in flight.
+template <int MODE>
+struct TcThreads {
+  static constexpr int EPI = ModeTraits<MODE>::rk_mid ? 8 : 16;
+  static constexpr int N = 64 + 32 * EPI;
+};
 
 template <int BN, int STAGES>
 struct TcCfg {
@@ -41,7 +50,7 @@ struct TcCfg {
 // (column block fastest), with two tensor-memory accumulators so that the
 // epilogue of one tile overlaps the MMAs of the next.
 template <int BN, int STAGES, bool CPLX, int MODE, bool F8>
-__global__ void __launch_bounds__(NTHREADS, 1)
+__global__ void __launch_bounds__(TcThreads<MODE>::N, 1)
     step_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int b_row0,
                    StepArgs a) {
   using Cfg = TcCfg<BN, STAGES>;
@@ -162,11 +171,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     // ---------------- epilogue warps ----------------
     constexpr int W = CPLX ? 2 : 1;
     constexpr int RPT = BN / W;
-    constexpr int CW = (ModeTraits<MODE>::rk_mid || !CPLX) ? 8 : 16;
-    constexpr int NCH = (BN / 2) / CW;
+    constexpr int NEPI = TcThreads<MODE>::EPI;
+    constexpr int NPART = NEPI / 4;  // column parts
+    constexpr int PW = BN / NPART;   // columns per part
+    constexpr int CW = (ModeTraits<MODE>::rk_mid || !CPLX || NPART > 2) ? 8 : 16;
+    constexpr int NCH = PW / CW;
+    static_assert(PW % CW == 0, "column part must hold whole chunks");
     const int e = threadIdx.x - 64;
     const int q = warp & 3;
-    const int half = (warp - 2) >> 2;
+    const int part = (warp - 2) >> 2;
     const bool need_red = MODE == M_ENERGY || ((MODE == M_EULER || MODE == M_RK4) && a.rho_out != nullptr);
     float* out = (MODE == M_ENERGY) ? a.e_part : ((MODE == M_EULER || MODE == M_RK4) ? a.rho_out : nullptr);
     int bad = 0;
@@ -179,7 +192,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const uint32_t use = lt >> 1;
       const int rbase = n0 / W;
       const int i = m0 + 32 * q + lane;
-      const int cbeg = n0 + half * (BN / 2);
+      const int cbeg = n0 + part * PW;
       // FP8: the accumulator holds (J0_ij / s_i)(psi_j / sigma); one product
       // with s_i sigma restores Y (sigma a power of two: exact).
       const float rs = F8 ? __fmul_rn(a.row_scale[i], kFp8PsiScale) : 1.0f;
@@ -190,7 +203,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         s_beta[e] = stage_beta(a, bt);
         s_dsc[e] = r < a.R ? noise_scale(a, r) : 0.0f;
       }
-      epi_bar_sync();
+      epi_bar_sync_n<32 * NEPI>();
       const bool ok = __all_sync(0xffffffffu, mbar_wait(acc_full(b), use & 1) && !*(volatile int*)&s_flag[0]);
       tc_fence_after();
       if (!ok) {
@@ -199,7 +212,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         break;
       }
       if (lt == 0 && e == 0) stamp(a, 4);
-      const uint32_t taddr = tmem + b * BN + (static_cast<uint32_t>(32 * q) << 16) + half * (BN / 2);
+      const uint32_t taddr = tmem + b * BN + (static_cast<uint32_t>(32 * q) << 16) + part * PW;
       auto body = [&](int ch, const EpiRegs<MODE, CPLX, CW>& cur, EpiRegs<MODE, CPLX, CW>& nxt) {
         if (ch + 1 < NCH) epi_load<MODE, CPLX, CW>(a, i, cbeg + (ch + 1) * CW, nxt);
         float v[CW];
@@ -208,7 +221,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
           for (int k = 0; k < CW; ++k) v[k] = __fmul_rn(v[k], rs);
         }
-        const int lr0 = (half * (BN / 2) + ch * CW) / W;
+        const int lr0 = (part * PW + ch * CW) / W;
         float red[CW / W];
         epi_chunk<MODE, CPLX, CW>(a, i, cbeg + ch * CW, v, cur, &s_beta[lr0], &s_dsc[lr0], red, bad);
         if (need_red) {
@@ -228,7 +241,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       }
       if (NCH & 1) body(NCH - 1, R[0], R[1]);
       tc_fence_before();
-      epi_bar_sync();
+      epi_bar_sync_n<32 * NEPI>();
       if (e == 0) mbar_arrive(acc_empty(b));  // accumulator b may be overwritten
       if (lt == 0 && e == 0) stamp(a, 5);
       if (e < RPT) {
@@ -241,7 +254,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       }
     }
     if (bad) s_flag[1] = 1;
-    epi_bar_sync();
+    epi_bar_sync_n<32 * NEPI>();
     if (e == 0 && s_flag[1]) atomicOr(a.err, E_DIVERGED);
     if (e == 0) stamp(a, 6);
   }
@@ -306,7 +319,7 @@ cudaError_t launch_cfg(const CUtensorMap& A, const CUtensorMap& B, int b_row0, c
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return cudaErrorUnknown;
   }
   const int tiles = ((a.C + BN - 1) / BN) * ((a.N + BM - 1) / BM);
-  kern<<<tiles < sms ? tiles : sms, NTHREADS, Cfg::SMEM, s>>>(A, B, b_row0, a);
+  kern<<<tiles < sms ? tiles : sms, TcThreads<MODE>::N, Cfg::SMEM, s>>>(A, B, b_row0, a);
   return cudaGetLastError();
 }
 

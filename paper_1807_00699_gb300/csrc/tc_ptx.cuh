@@ -159,6 +159,11 @@ static __device__ __forceinline__ void tmem_ld(uint32_t taddr, float* v) {
 }
 
 static __device__ __forceinline__ void epi_bar_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+// Named barrier 1 over the N epilogue threads.
+template <int N>
+static __device__ __forceinline__ void epi_bar_sync_n() {
+  asm volatile("bar.sync 1, %0;" ::"n"(N) : "memory");
+}
 
 
 // tcgen05.st of 16 / 8 columns (row = lane base + lane), then wait.
