@@ -38,15 +38,16 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="bf16", choices=["bf16", "fp32", "fp8"])
+    ap.add_argument("--prec", default="bf16", choices=["bf16", "fp32", "fp8", "sparse"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32-ttt", action="store_true")
     ap.add_argument("--workload", default="xy1000", choices=["xy1000", "batched", "sk4096", "kernel"],
                     help="xy1000: the headline workload; batched: the 2000-instance serving mix; "
                          "sk4096: SK N=4096 R=4096 quality per precision (FP32 / BF16 / FP8); "
                          "kernel: time per step of one configuration (the small cases profiled with ncu)")
-    ap.add_argument("--model", default="xy", choices=["xy", "ising"], help="kernel workload: XY (J ~ N(0, 1/N)) "
-                    "or Ising SK (J ~ N(0, 1))")
+    ap.add_argument("--model", default="xy", choices=["xy", "ising", "ising3r"],
+                    help="kernel workload: XY (J ~ N(0, 1/N)), Ising SK (J ~ N(0, 1)) or Ising on the paper's "
+                         "sparse 3-regular graphs (weights U[a, b], a, b in {-10, -3, 3, 10})")
     ap.add_argument("--n", type=int, default=1000, help="kernel workload: spins")
     ap.add_argument("--r", type=int, default=1024, help="kernel workload: restarts")
     ap.add_argument("--sched", default="auto", choices=["auto", "per_step", "resident"])
@@ -180,6 +181,9 @@ def run_ours(args):
 
     W = WORKLOAD
     J, g = instance()
+    if args.prec == "sparse":
+        raise SystemExit("the headline XY instance is dense: time the sparse product with "
+                         "--workload kernel --model ising3r --prec sparse")
     prec = {"fp32": gda.FP32, "bf16": gda.BF16, "fp8": gda.FP8}[args.prec]
     stream = torch.cuda.Stream()
     s = gda.Solver(J, g, gda.XY, stream=stream)
@@ -263,8 +267,12 @@ def run_ours(args):
     kname = {gda.BF16: "step_res_kernel (resident: GEMM + fused epilogue, state in TMEM), time per step",
              gda.FP8: "step_tc_kernel (per-step, E4M3 operands), time per step",
              gda.FP32: "step_simt_kernel"}[prec]
+    # DRAM bytes per step of the resident kernel from the committed ncu capture of an
+    # 8-step launch (19.08 MB read + 0.04 MB written, all of it the cold start of the
+    # launch: J, state; HBM is idle in steady state)
+    traffic = (19.076e6 + 0.039e6) / 8 if prec == gda.BF16 else None
     roofline = {"bound": "alu" if prec == gda.FP32 else "tensor", "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None, "kernel": kname,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic, "kernel": kname,
                 "peak_source": src, "us_per_launch": t_kernel * 1e6}
 
     # end to end through host buffers: load J, solve, read the best configuration back
@@ -334,6 +342,25 @@ def run_ours(args):
                         "ttt_s_bf16_learned": first_hit(learned[1], learned[2], learned[3], learned[4]),
                         "learned_settings": learned[5], "proposal_s": learned[4]})
 
+    # the paper's XY integrator: classical RK4 on the same instance and start
+    # (per-step launches, four stages per step; one RK4 step counts once)
+    rk4 = None
+    if rank == 0 and prec != gda.FP32:
+        p4 = gda.default_params(dt=W["dt"], eps=W["eps"], rho_th=W["rho_th"], init_mode=1, init_amp=W["init_amp"],
+                                seed=seed, energy_every=W["energy_every"], prec=prec, integ=gda.RK4)
+        s.run(p4, W["R"], 20)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        s.run(p4, W["R"], W["steps"])
+        E4, _, _ = s.best(with_cfg=False)
+        e1.record(stream)
+        e1.synchronize()
+        t4 = e0.elapsed_time(e1) / 1e3
+        rk4 = {"solve_s": t4, "spin_updates_per_s": W["N"] * W["R"] * W["steps"] / t4, "E_best_fp64": E4,
+               "ms_per_step": t4 / W["steps"] * 1e3, "schedule": "per-step (4 launches per step)"}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = oracle_sample(12.0)
@@ -344,7 +371,8 @@ def run_ours(args):
                 "config": {"workload": W["name"], "model": "xy", "N": W["N"], "R": W["R"], "steps": W["steps"],
                            "integrator": "euler", "dt": W["dt"], "energy_every": W["energy_every"],
                            "l2": "flushed (256 MB write) between timed steps", "parallelism": f"replicas{world}"},
-                "time_to_target": ttt, "clocks": clocks.summary(), "roofline": roofline, "cpu_baseline": cpu,
+                "time_to_target": ttt, "rk4": rk4, "clocks": clocks.summary(), "roofline": roofline,
+                "cpu_baseline": cpu,
                 "e2e": {"value": units / e2e_t, "unit": "spin-updates/s", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
                 "gpu_launches": int(launches)}
@@ -534,15 +562,19 @@ def run_kernel(args):
     if args.model == "xy":
         J, g = synth.xy_gaussian(N, 1)
         dt = 0.05
+    elif args.model == "ising3r":
+        J, g = synth.sparse_3regular(N, 1)
+        dt = 0.005
     else:
         J, g = synth.sk_gaussian(N, 1)
         dt = 0.1 / math.sqrt(N)
-    prec = {"fp32": gda.FP32, "bf16": gda.BF16, "fp8": gda.FP8}[args.prec]
+    prec = {"fp32": gda.FP32, "bf16": gda.BF16, "fp8": gda.FP8, "sparse": gda.SPARSE}[args.prec]
     sched = {"auto": gda.AUTO, "per_step": gda.PER_STEP, "resident": gda.RESIDENT}[args.sched]
     integ = gda.RK4 if args.integ == "rk4" else gda.EULER
     stream = torch.cuda.Stream()
     s = gda.Solver(J, g, gda.XY if args.model == "xy" else gda.ISING, stream=stream)
     kw = dict(dt=dt, eps=0.1, prec=prec, schedule=sched, integ=integ)
+    del J  # the context holds its own copies
     gdmod = args.coupling == "gdmod"
     if gdmod:  # gamma_c above the coupling scale keeps Delta > 0 (2 for XY, 2 sqrt(N) for SK);
         # Delta(0) K(0) = 2 gamma_c beta0 J = 0.6 J
@@ -564,6 +596,10 @@ def run_kernel(args):
     line = {"workload": "kernel", "model": args.model, "N": N, "R": R, "prec": args.prec, "sched": args.sched,
             "integ": args.integ, "coupling": args.coupling, "steps": args.kernel_steps, "us_per_step": t * 1e6,
             "tflops": flops / t / 1e12, "spin_updates_per_s": N * R / t}
+    if prec == gda.SPARSE:  # FP32 state read and written once per step (gathers hit L1 / L2)
+        line["tflops"] = None
+        line["state_bytes_per_step"] = 8 * N * (C + R) * (4 if integ == gda.RK4 else 1)
+        line["gbs"] = line["state_bytes_per_step"] / t / 1e9
     if gdmod:  # K read and written once per step: 8 bytes per element of R x N x Np
         Np = (N + 127) // 128 * 128
         line["tflops"] = None

@@ -64,13 +64,23 @@ typedef enum { GDA_EULER = 0, GDA_RK4 = 1 } gda_integrator;
 typedef enum {
   GDA_FP32 = 0, /* J.Psi on CUDA cores in FP32 (the plain reference path)     */
   GDA_BF16 = 1, /* J.Psi on tcgen05 tensor cores, BF16 operands, FP32 accum   */
-  GDA_FP8 = 2   /* J.Psi on tcgen05 tensor cores, E4M3 operands, FP32 accum:
+  GDA_FP8 = 2,  /* J.Psi on tcgen05 tensor cores, E4M3 operands, FP32 accum:
                  * J0_ij stored as e4m3(J0_ij / s_i), s_i = max_j |J0_ij| / 448
                  * (row scale), amplitudes as e4m3(psi * 64) (|psi| up to 7
                  * before saturation), Y_i = acc_i * s_i / 64.  Per-step
                  * schedule only; the energy tracking of energy_every uses
                  * the BF16 product of the projected spins. */
+  GDA_SPARSE = 3 /* J.Psi over the nonzeros of J only (the paper's sparse
+                 * 3-regular instances, Sec. 2): on first use J0 is compacted
+                 * on the device into an ELL table of at most
+                 * GDA_SPARSE_MAX_DEG nonzeros per row (column index and FP32
+                 * value, ascending column order); every step gathers those
+                 * entries on CUDA cores in FP32.  Amplitudes, gains, noise
+                 * (with decay), RK4 and the energy tracking as in GDA_FP32.
+                 * A row with more nonzeros gives GDA_ERR_UNSUPPORTED. */
 } gda_precision;
+
+#define GDA_SPARSE_MAX_DEG 64
 
 /* Run parameters (Eqs. 2, 5, 6; Sec. 2 integrator).  Fill with
  * gda_default_params, then override.  All rates are per unit of time t. */

@@ -62,6 +62,12 @@ struct gda_ctx {
   __nv_bfloat16* ops = nullptr;  // [3][Cp][Np]: operand ping-pong + projected spins
   unsigned char* ops8 = nullptr;  // [2][Cp][Np]: E4M3 operand ping-pong (FP8 path)
   TcPlan* plan8 = nullptr;
+  int* ell_col = nullptr;     // sparse J0: [GDA_SPARSE_MAX_DEG][Np] column indices
+  float* ell_val = nullptr;   // [GDA_SPARSE_MAX_DEG][Np] values
+  int* ell_deg = nullptr;     // [Np] nonzeros per row
+  int* d_maxdeg = nullptr;
+  int ell_maxdeg = -1;        // largest row count of the current J (-1: not built)
+  bool run_sparse = false;    // steps of the current call use the sparse product
   float* K = nullptr;  // GD-mod per-restart couplings [K_R][N][Np]
   size_t K_cap = 0;
   int K_R = 0;         // restarts K was initialised for (0: none)
@@ -216,6 +222,7 @@ gda_status load_instance(gda_ctx* c, const double* J, const double* g, cudaMemcp
   CK(cudaMemsetAsync(c->g64, 0, Np * sizeof(double), c->stream));
   if (g) CK(cudaMemcpyAsync(c->g64, g, N * sizeof(double), kind, c->stream));
   c->K_R = 0;  // a GD-mod coupling state belongs to the previous J
+  c->ell_maxdeg = -1;
   CK(cudaMemsetAsync(c->d_flags, 0, sizeof(int), c->stream));
   CK(cudaMemsetAsync(c->d_maxabs, 0, sizeof(unsigned long long), c->stream));
   LK(launch_check_instance(c->J64, c->g64, c->N, c->Np, c->d_flags, c->d_maxabs, c->d_diag, c->stream));
@@ -240,6 +247,33 @@ gda_status load_instance(gda_ctx* c, const double* J, const double* g, cudaMemcp
   }
   LK(launch_prepare_J(c->J64, c->Np, c->J32, c->J16, c->int_exact ? c->Jint : nullptr, c->stream));
   c->j8_ready = false;
+  return GDA_OK;
+}
+
+// Sparse J0 on first use: the ELL table of the nonzeros (at most
+// GDA_SPARSE_MAX_DEG per row).  Synchronises once to read the largest count.
+gda_status ensure_ell(gda_ctx* c) {
+  const size_t Np = c->Np;
+  if (!c->ell_col) {
+    CK(dalloc(&c->ell_col, size_t(GDA_SPARSE_MAX_DEG) * Np));
+    CK(dalloc(&c->ell_val, size_t(GDA_SPARSE_MAX_DEG) * Np));
+    CK(dalloc(&c->ell_deg, Np));
+    CK(dalloc(&c->d_maxdeg, 1));
+  }
+  if (c->ell_maxdeg < 0) {
+    CK(cudaMemsetAsync(c->ell_col, 0, size_t(GDA_SPARSE_MAX_DEG) * Np * sizeof(int), c->stream));
+    CK(cudaMemsetAsync(c->ell_val, 0, size_t(GDA_SPARSE_MAX_DEG) * Np * sizeof(float), c->stream));
+    CK(cudaMemsetAsync(c->d_maxdeg, 0, sizeof(int), c->stream));
+    LK(launch_prepare_ell(c->J32, c->N, int(Np), GDA_SPARSE_MAX_DEG, c->ell_col, c->ell_val, c->ell_deg,
+                          c->d_maxdeg, c->stream));
+    int m = 0;
+    CK(cudaMemcpyAsync(&m, c->d_maxdeg, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->ell_maxdeg = m;
+  }
+  if (c->ell_maxdeg > GDA_SPARSE_MAX_DEG)
+    return fail(c, GDA_ERR_UNSUPPORTED, "J has %d nonzeros in a row; the sparse product takes at most %d",
+                c->ell_maxdeg, GDA_SPARSE_MAX_DEG);
   return GDA_OK;
 }
 
@@ -269,7 +303,7 @@ bool finite(double x) { return std::isfinite(x); }
 gda_status check_params(gda_ctx* c, const gda_params* p) {
   if (!p) return fail(c, GDA_ERR_INVALID, "params is NULL");
   if (p->integ != GDA_EULER && p->integ != GDA_RK4) return fail(c, GDA_ERR_INVALID, "unknown integrator %d", p->integ);
-  if (p->prec != GDA_FP32 && p->prec != GDA_BF16 && p->prec != GDA_FP8)
+  if (p->prec != GDA_FP32 && p->prec != GDA_BF16 && p->prec != GDA_FP8 && p->prec != GDA_SPARSE)
     return fail(c, GDA_ERR_INVALID, "unknown precision %d", p->prec);
   const double v[] = {p->dt, p->eps, p->rho_th, p->gamma0, p->beta0, p->eps_hat, p->noise_D, p->init_amp};
   for (double x : v)
@@ -282,8 +316,10 @@ gda_status check_params(gda_ctx* c, const gda_params* p) {
   if (p->energy_every < 0) return fail(c, GDA_ERR_INVALID, "energy_every must be >= 0");
   if (p->schedule < GDA_SCHEDULE_AUTO || p->schedule > GDA_SCHEDULE_RESIDENT)
     return fail(c, GDA_ERR_INVALID, "unknown schedule %d", p->schedule);
-  if (p->prec != GDA_FP32 && !c->tc_ok)
+  if ((p->prec == GDA_BF16 || p->prec == GDA_FP8) && !c->tc_ok)
     return fail(c, GDA_ERR_UNSUPPORTED, "tensor-core path needs an sm_103 device");
+  if (p->prec == GDA_SPARSE && p->schedule == GDA_SCHEDULE_RESIDENT)
+    return fail(c, GDA_ERR_UNSUPPORTED, "the sparse product runs per step");
   if (p->coupling != GDA_COUPLING_GD && p->coupling != GDA_COUPLING_GDMOD)
     return fail(c, GDA_ERR_INVALID, "unknown coupling mode %d", p->coupling);
   if (p->coupling == GDA_COUPLING_GDMOD) {
@@ -317,7 +353,9 @@ StepArgs base_args(gda_ctx* c, const gda_params* p, bool tc) {
 }
 
 gda_status launch_step(gda_ctx* c, const StepArgs& a, bool tc, const float* operand32, int op_buf) {
-  if (a.row_scale) {
+  if (c->run_sparse && !tc) {
+    LK(launch_step_sparse(a, c->ell_col, c->ell_val, c->ell_deg, operand32, c->stream));
+  } else if (a.row_scale) {
     LK(launch_step_tc8(c->plan8, a, op_buf, c->stream));
   } else if (tc) {
     LK(launch_step_tc(c->plan, a, op_buf, c->stream));
@@ -461,6 +499,7 @@ void gda_destroy(gda_ctx* c) {
   dfree(c->t_step); dfree(c->t_E); dfree(c->t_r); dfree(c->t_count); dfree(c->err); dfree(c->flags);
   dfree(c->stamps);
   dfree(c->K);
+  dfree(c->ell_col); dfree(c->ell_val); dfree(c->ell_deg); dfree(c->d_maxdeg);
   dfree(c->fw[0]);
   dfree(c->fw[1]);
   dfree(c->base);
@@ -564,8 +603,14 @@ gda_status gda_run(gda_ctx* c, const gda_params* p, int32_t R, int64_t steps) {
   if (R < 1) return fail(c, GDA_ERR_INVALID, "R must be >= 1");
   if (steps < 0) return fail(c, GDA_ERR_INVALID, "steps must be >= 0");
   if (size_t(c->cplx ? 2 : 1) * size_t(R) > size_t(1) << 24) return fail(c, GDA_ERR_INVALID, "R too large");
-  const bool tc = p->prec != GDA_FP32;
+  const bool tc = p->prec == GDA_BF16 || p->prec == GDA_FP8;
   const bool f8 = p->prec == GDA_FP8;
+  c->run_sparse = false;
+  if (p->prec == GDA_SPARSE && p->coupling != GDA_COUPLING_GDMOD) {
+    s = ensure_ell(c);
+    if (s != GDA_OK) return s;
+    c->run_sparse = true;
+  }
   if (p->init_mode == 2) {
     if (!c->have_state || c->R != R) return fail(c, GDA_ERR_STATE, "init_mode 2 needs a state with the same R");
   } else {
@@ -854,11 +899,18 @@ gda_status gda_features(gda_ctx* c, float* F) {
 gda_status gda_coupling(gda_ctx* c, int32_t prec, int32_t R, const float* X, float* Y) {
   if (!c) return GDA_ERR_INVALID;
   if (!X || !Y || R < 1) return fail(c, GDA_ERR_INVALID, "X or Y NULL, or R < 1");
-  if (prec != GDA_FP32 && prec != GDA_BF16 && prec != GDA_FP8) return fail(c, GDA_ERR_INVALID, "unknown precision");
-  if (prec != GDA_FP32 && !c->tc_ok) return fail(c, GDA_ERR_UNSUPPORTED, "tensor-core path needs an sm_103 device");
+  if (prec != GDA_FP32 && prec != GDA_BF16 && prec != GDA_FP8 && prec != GDA_SPARSE)
+    return fail(c, GDA_ERR_INVALID, "unknown precision");
+  const bool tc = prec == GDA_BF16 || prec == GDA_FP8;
+  if (tc && !c->tc_ok) return fail(c, GDA_ERR_UNSUPPORTED, "tensor-core path needs an sm_103 device");
+  c->run_sparse = false;
+  if (prec == GDA_SPARSE) {
+    gda_status se = ensure_ell(c);
+    if (se != GDA_OK) return se;
+    c->run_sparse = true;
+  }
   gda_status s = gda_set_state(c, X, nullptr, nullptr, R, 0);
   if (s != GDA_OK) return s;
-  const bool tc = prec != GDA_FP32;
   gda_params p;
   gda_default_params(&p);
   StepArgs a = base_args(c, &p, tc);

@@ -82,6 +82,12 @@ __device__ __forceinline__ void stamp(const StepArgs& a, int k) {
 // Launchers (return cudaGetLastError() of the launch).
 cudaError_t launch_step_simt(const StepArgs& a, const float* J32, const float* operand, cudaStream_t s);
 int simt_mtiles(int N);
+// Sparse J0 (ELL [dmax][Np], ascending columns): the SIMT step with the SGEMM
+// replaced by a gather over the nonzeros; same tiles and epilogue.
+cudaError_t launch_step_sparse(const StepArgs& a, const int* col, const float* val, const int* deg,
+                               const float* operand, cudaStream_t s);
+cudaError_t launch_prepare_ell(const float* J32, int N, int Np, int dmax, int* col, float* val, int* deg, int* maxdeg,
+                               cudaStream_t s);
 
 struct TcPlan;  // opaque plan holding the tensor maps of one context
 cudaError_t tc_plan_create(TcPlan** plan, const __nv_bfloat16* J16, int Np,

@@ -2,6 +2,13 @@
 // (spins i) x (columns c), fused with the step epilogue (Eqs. 2, 5, 6).  This
 // is the plain FP32 path the tensor-core path is measured against, and the
 // path whose amplitudes are compared with the FP64 oracle.
+//
+// The sparse variant (SPARSE = true) replaces the SGEMM by a gather over the
+// nonzeros of J0 in ELL form (col / val [dmax][Np], deg [Np]): thread (tx, ty)
+// sums, for its 4 rows and 4 columns, val_ik X[c][col_ik] in ascending k.  The
+// tile shape, the thread-to-element map and the epilogue (with its partial-sum
+// order) are the dense kernel's, so density partials, noise decay and the
+// energy mode carry over unchanged.
 #include "epilogue.cuh"
 
 namespace gda {
@@ -9,11 +16,17 @@ namespace {
 
 constexpr int BM = 64, BN = 64, BK = 16, PAD = 4;
 
-template <bool CPLX>
+struct Ell {
+  const int* col;   // [dmax][Np]
+  const float* val; // [dmax][Np]
+  const int* deg;   // [Np], 0 beyond N
+};
+
+template <bool CPLX, bool SPARSE>
 __global__ void __launch_bounds__(256) step_simt_kernel(StepArgs a, const float* __restrict__ J,
-                                                        const float* __restrict__ X) {
-  __shared__ __align__(16) float As[BK][BM + PAD];
-  __shared__ __align__(16) float Bs[BK][BN + PAD];
+                                                        const float* __restrict__ X, Ell ell) {
+  __shared__ __align__(16) float As[SPARSE ? 1 : BK][BM + PAD];
+  __shared__ __align__(16) float Bs[SPARSE ? 1 : BK][BN + PAD];
   __shared__ float s_beta[BN], s_dsc[BN];
   __shared__ int s_bad;
 
@@ -33,10 +46,25 @@ __global__ void __launch_bounds__(256) step_simt_kernel(StepArgs a, const float*
   }
 
   float acc[4][4] = {};
+  if (SPARSE) {
+    const int cq = n0 + 4 * ty;  // the thread's 4 columns (always < Cp)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int i = m0 + tx + 16 * q;
+      const int d = i < a.N ? ell.deg[i] : 0;
+      for (int k = 0; k < d; ++k) {
+        const size_t o = size_t(k) * Np + i;
+        const int j = ell.col[o];
+        const float v = ell.val[o];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[q][u] = __fmaf_rn(v, X[size_t(cq + u) * Np + j], acc[q][u]);
+      }
+    }
+  }
   const int lr = tid >> 2, lk = (tid & 3) * 4;
-  const float* Jp = J + size_t(m0 + lr) * Np + lk;
-  const float* Xp = X + size_t(n0 + lr) * Np + lk;
-  for (int k0 = 0; k0 < Np; k0 += BK) {
+  const float* Jp = SPARSE ? nullptr : J + size_t(m0 + lr) * Np + lk;
+  const float* Xp = SPARSE ? nullptr : X + size_t(n0 + lr) * Np + lk;
+  for (int k0 = 0; !SPARSE && k0 < Np; k0 += BK) {
     const float4 av = *reinterpret_cast<const float4*>(Jp + k0);
     const float4 bv = *reinterpret_cast<const float4*>(Xp + k0);
     __syncthreads();
@@ -100,10 +128,62 @@ int simt_mtiles(int N) { return (N + BM - 1) / BM; }
 
 cudaError_t launch_step_simt(const StepArgs& a, const float* J32, const float* operand, cudaStream_t s) {
   dim3 grid((a.C + BN - 1) / BN, simt_mtiles(a.N));
+  const Ell none{nullptr, nullptr, nullptr};
   if (a.cplx)
-    step_simt_kernel<true><<<grid, 256, 0, s>>>(a, J32, operand);
+    step_simt_kernel<true, false><<<grid, 256, 0, s>>>(a, J32, operand, none);
   else
-    step_simt_kernel<false><<<grid, 256, 0, s>>>(a, J32, operand);
+    step_simt_kernel<false, false><<<grid, 256, 0, s>>>(a, J32, operand, none);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_step_sparse(const StepArgs& a, const int* col, const float* val, const int* deg,
+                               const float* operand, cudaStream_t s) {
+  dim3 grid((a.C + BN - 1) / BN, simt_mtiles(a.N));
+  const Ell ell{col, val, deg};
+  if (a.cplx)
+    step_simt_kernel<true, true><<<grid, 256, 0, s>>>(a, nullptr, operand, ell);
+  else
+    step_simt_kernel<false, true><<<grid, 256, 0, s>>>(a, nullptr, operand, ell);
+  return cudaGetLastError();
+}
+
+namespace {
+
+// One warp per row of J0 (FP32, diagonal removed, zero padding): the nonzeros
+// of row i in ascending column order go to col / val [k][Np] for k < dmax;
+// deg[i] = min(count, dmax) and *maxdeg receives the largest count.
+__global__ void k_prepare_ell(const float* __restrict__ J32, int N, int Np, int dmax, int* col, float* val, int* deg,
+                              int* maxdeg) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= Np) return;
+  const int i = warp;
+  int count = 0;
+  if (i < N) {
+    const float* row = J32 + size_t(i) * Np;
+    for (int j0 = 0; j0 < N; j0 += 32) {
+      const int j = j0 + lane;
+      const float v = j < N ? row[j] : 0.0f;
+      const unsigned m = __ballot_sync(0xffffffffu, v != 0.0f);
+      const int k = count + __popc(m & ((1u << lane) - 1u));
+      if (v != 0.0f && k < dmax) {
+        col[size_t(k) * Np + i] = j;
+        val[size_t(k) * Np + i] = v;
+      }
+      count += __popc(m);
+    }
+  }
+  if (lane == 0) {
+    deg[i] = count < dmax ? count : dmax;
+    atomicMax(maxdeg, count);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_prepare_ell(const float* J32, int N, int Np, int dmax, int* col, float* val, int* deg, int* maxdeg,
+                               cudaStream_t s) {
+  const int blocks = (Np * 32 + 255) / 256;
+  k_prepare_ell<<<blocks, 256, 0, s>>>(J32, N, Np, dmax, col, val, deg, maxdeg);
   return cudaGetLastError();
 }
 

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_HERE, "libgda.so")
 
 ISING, XY = 0, 1
 EULER, RK4 = 0, 1
-FP32, BF16, FP8 = 0, 1, 2
+FP32, BF16, FP8, SPARSE = 0, 1, 2, 3
 GD, GDMOD = 0, 1  # coupling feedback (gda_coupling_mode)
 AUTO, PER_STEP, RESIDENT = 0, 1, 2
 
