@@ -27,7 +27,8 @@ namespace gda {
 namespace {
 
 using namespace ptx;
-constexpr int NTHREADS = 320;
+constexpr int NEPI = 16;  // epilogue warps: 4 column parts x 4 lane quarters
+constexpr int NTHREADS = 64 + 32 * NEPI;
 
 struct BatchInst {
   int N, Np, C, R, Cp, Rp, mt;
@@ -70,7 +71,7 @@ struct BCfg {
   static constexpr uint32_t SMEM = 1024 + STAGES * STAGE_BYTES + TAIL;
 };
 
-__device__ __forceinline__ void bar_epi() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+__device__ __forceinline__ void bar_epi() { asm volatile("bar.sync 1, %0;" ::"n"(32 * NEPI) : "memory"); }
 
 // StepArgs of one instance for a forward-Euler step with parity cur.
 __device__ __forceinline__ StepArgs unit_args(const BatchArgs& b, const BatchInst& I, unsigned step, int cur) {
@@ -210,11 +211,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   } else {
     constexpr int W = CPLX ? 2 : 1;
     constexpr int RPT = BN / W;
-    constexpr int CW = CPLX ? 16 : 8;
-    constexpr int NCH = (BN / 2) / CW;
+    constexpr int PW = BN / (NEPI / 4);  // columns per part
+    constexpr int CW = 8;
+    constexpr int NCH = PW / CW;
+    static_assert(PW % CW == 0, "column part must hold whole chunks");
     const int e = threadIdx.x - 64;
     const int q = warp & 3;
-    const int half = (warp - 2) >> 2;
+    const int part = (warp - 2) >> 2;
     int bad = 0, lt = 0;
     EpiRegs<M_EULER, CPLX, CW> R[2];
     for (int u = u0; u < u1; ++u, ++lt) {
@@ -226,7 +229,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const uint32_t use = lt >> 1;
       const int rbase = n0 / W;
       const int i = m0 + 32 * q + lane;
-      const int cbeg = n0 + half * (BN / 2);
+      const int cbeg = n0 + part * PW;
       epi_load<M_EULER, CPLX, CW>(a, i, cbeg, R[0]);
       if (e < RPT) {
         const int r = rbase + e;
@@ -241,12 +244,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         atomicOr(&s_flag[0], 1);
         break;
       }
-      const uint32_t taddr = tmem + k2 * BN + (static_cast<uint32_t>(32 * q) << 16) + half * (BN / 2);
+      const uint32_t taddr = tmem + k2 * BN + (static_cast<uint32_t>(32 * q) << 16) + part * PW;
       auto body = [&](int ch, const EpiRegs<M_EULER, CPLX, CW>& cr, EpiRegs<M_EULER, CPLX, CW>& nx) {
         if (ch + 1 < NCH) epi_load<M_EULER, CPLX, CW>(a, i, cbeg + (ch + 1) * CW, nx);
         float v[CW];
         tmem_ld<CW>(taddr + ch * CW, v);
-        const int lr0 = (half * (BN / 2) + ch * CW) / W;
+        const int lr0 = (part * PW + ch * CW) / W;
         float red[CW / W];
         epi_chunk<M_EULER, CPLX, CW>(a, i, cbeg + ch * CW, v, cr, &s_beta[lr0], &s_dsc[lr0], red, bad);
       };
