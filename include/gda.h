@@ -129,7 +129,15 @@ typedef enum { GDA_COUPLING_GD = 0, GDA_COUPLING_GDMOD = 1 } gda_coupling_mode;
 typedef enum {
   GDA_SCHEDULE_AUTO = 0,
   GDA_SCHEDULE_PER_STEP = 1,
-  GDA_SCHEDULE_RESIDENT = 2 /* GDA_ERR_UNSUPPORTED if not applicable */
+  GDA_SCHEDULE_RESIDENT = 2, /* GDA_ERR_UNSUPPORTED if not applicable */
+  GDA_SCHEDULE_PAIR = 3      /* per-step launches with two-SM tiles: clusters of
+                              * two CTAs share 256 x BN tensor-core tiles
+                              * (tcgen05 cta_group::2), each SM staging its 128
+                              * rows of J and half of the operand columns;
+                              * BF16 / FP8 only, N rounded up to 128 must be a
+                              * multiple of 256, else GDA_ERR_UNSUPPORTED.
+                              * AUTO uses them for per-step runs whose pair
+                              * tiles fill three or more waves of clusters */
 } gda_schedule;
 
 /* Fills p with dt = 0.01, eps = 0.1, rho_th = 1, gamma0 = 0, beta0 = 1,

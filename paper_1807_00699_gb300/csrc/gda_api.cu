@@ -68,6 +68,7 @@ struct gda_ctx {
   int* d_maxdeg = nullptr;
   int ell_maxdeg = -1;        // largest row count of the current J (-1: not built)
   bool run_sparse = false;    // steps of the current call use the sparse product
+  bool run_pair = false;      // tensor-core launches of the current call use two-SM tiles
   float* K = nullptr;  // GD-mod per-restart couplings [K_R][N][Np]
   size_t K_cap = 0;
   int K_R = 0;         // restarts K was initialised for (0: none)
@@ -314,12 +315,15 @@ gda_status check_params(gda_ctx* c, const gda_params* p) {
   if (p->init_mode < 0 || p->init_mode > 3) return fail(c, GDA_ERR_INVALID, "init_mode must be 0, 1, 2 or 3");
   if (p->init_mode == 3 && !c->base) return fail(c, GDA_ERR_STATE, "init_mode 3 needs gda_set_init_base first");
   if (p->energy_every < 0) return fail(c, GDA_ERR_INVALID, "energy_every must be >= 0");
-  if (p->schedule < GDA_SCHEDULE_AUTO || p->schedule > GDA_SCHEDULE_RESIDENT)
+  if (p->schedule < GDA_SCHEDULE_AUTO || p->schedule > GDA_SCHEDULE_PAIR)
     return fail(c, GDA_ERR_INVALID, "unknown schedule %d", p->schedule);
   if ((p->prec == GDA_BF16 || p->prec == GDA_FP8) && !c->tc_ok)
     return fail(c, GDA_ERR_UNSUPPORTED, "tensor-core path needs an sm_103 device");
   if (p->prec == GDA_SPARSE && p->schedule == GDA_SCHEDULE_RESIDENT)
     return fail(c, GDA_ERR_UNSUPPORTED, "the sparse product runs per step");
+  if (p->schedule == GDA_SCHEDULE_PAIR &&
+      (!(p->prec == GDA_BF16 || p->prec == GDA_FP8) || (c->Np / 128) % 2 != 0 || p->coupling != GDA_COUPLING_GD))
+    return fail(c, GDA_ERR_UNSUPPORTED, "two-SM tiles need BF16 or FP8 and an even number of 128-row blocks");
   if (p->coupling != GDA_COUPLING_GD && p->coupling != GDA_COUPLING_GDMOD)
     return fail(c, GDA_ERR_INVALID, "unknown coupling mode %d", p->coupling);
   if (p->coupling == GDA_COUPLING_GDMOD) {
@@ -356,9 +360,9 @@ gda_status launch_step(gda_ctx* c, const StepArgs& a, bool tc, const float* oper
   if (c->run_sparse && !tc) {
     LK(launch_step_sparse(a, c->ell_col, c->ell_val, c->ell_deg, operand32, c->stream));
   } else if (a.row_scale) {
-    LK(launch_step_tc8(c->plan8, a, op_buf, c->stream));
+    LK(launch_step_tc8(c->plan8, a, op_buf, c->stream, c->run_pair));
   } else if (tc) {
-    LK(launch_step_tc(c->plan, a, op_buf, c->stream));
+    LK(launch_step_tc(c->plan, a, op_buf, c->stream, c->run_pair));
   } else {
     LK(launch_step_simt(a, c->J32, operand32, c->stream));
   }
@@ -606,6 +610,7 @@ gda_status gda_run(gda_ctx* c, const gda_params* p, int32_t R, int64_t steps) {
   const bool tc = p->prec == GDA_BF16 || p->prec == GDA_FP8;
   const bool f8 = p->prec == GDA_FP8;
   c->run_sparse = false;
+  c->run_pair = p->schedule == GDA_SCHEDULE_PAIR;
   if (p->prec == GDA_SPARSE && p->coupling != GDA_COUPLING_GDMOD) {
     s = ensure_ell(c);
     if (s != GDA_OK) return s;
@@ -649,11 +654,12 @@ gda_status gda_run(gda_ctx* c, const gda_params* p, int32_t R, int64_t steps) {
   const size_t opsz = cn;
   // Resident persistent kernel: BF16 Euler runs whose tiles all fit on the
   // device at once run as one launch per tracking segment.
-  const bool resident = p->prec == GDA_BF16 && p->integ == GDA_EULER && p->schedule != GDA_SCHEDULE_PER_STEP &&
+  const bool resident = p->prec == GDA_BF16 && p->integ == GDA_EULER && (p->schedule == GDA_SCHEDULE_AUTO || p->schedule == GDA_SCHEDULE_RESIDENT) &&
                         res_fits(c->N, c->C, c->dev) &&
                         (long long)((c->C + 127) / 128) * ((c->N + 127) / 128) <= kMaxResidentTiles;
   if (p->schedule == GDA_SCHEDULE_RESIDENT && !resident)
     return fail(c, GDA_ERR_UNSUPPORTED, "resident schedule needs BF16, Euler and a grid that fits the device");
+  if (tc && !resident && p->schedule == GDA_SCHEDULE_AUTO && tc_pair_pays(c->N, c->C)) c->run_pair = true;
   if (resident) {
     const int64_t seg = p->energy_every > 0 ? p->energy_every : steps;
     for (int64_t k = 0; k < steps; k += seg) {
@@ -904,6 +910,7 @@ gda_status gda_coupling(gda_ctx* c, int32_t prec, int32_t R, const float* X, flo
   const bool tc = prec == GDA_BF16 || prec == GDA_FP8;
   if (tc && !c->tc_ok) return fail(c, GDA_ERR_UNSUPPORTED, "tensor-core path needs an sm_103 device");
   c->run_sparse = false;
+  c->run_pair = false;
   if (prec == GDA_SPARSE) {
     gda_status se = ensure_ell(c);
     if (se != GDA_OK) return se;

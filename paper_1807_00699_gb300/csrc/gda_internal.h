@@ -93,12 +93,14 @@ struct TcPlan;  // opaque plan holding the tensor maps of one context
 cudaError_t tc_plan_create(TcPlan** plan, const __nv_bfloat16* J16, int Np,
                            const __nv_bfloat16* ops, int n_op_bufs, int Cp);
 void tc_plan_destroy(TcPlan* plan);
-cudaError_t launch_step_tc(const TcPlan* plan, const StepArgs& a, int op_buf, cudaStream_t s);
+// pair: two-SM tiles (cta_group::2, clusters of 2 CTAs); needs an even number
+// of 128-row blocks (cudaErrorInvalidValue otherwise).
+cudaError_t launch_step_tc(const TcPlan* plan, const StepArgs& a, int op_buf, cudaStream_t s, bool pair = false);
 // FP8 operands (E4M3 J with per-row scales, E4M3 amplitudes at a fixed scale):
 // plan over J8 [Np][Np] and ops8 [n_op_bufs * Cp][Np] (bytes).
 cudaError_t tc_plan8_create(TcPlan** plan, const unsigned char* J8, int Np, const unsigned char* ops8, int n_op_bufs,
                             int Cp);
-cudaError_t launch_step_tc8(const TcPlan* plan, const StepArgs& a, int op_buf, cudaStream_t s);
+cudaError_t launch_step_tc8(const TcPlan* plan, const StepArgs& a, int op_buf, cudaStream_t s, bool pair = false);
 constexpr float kFp8PsiScale = 1.0f / 64.0f;
 // J8_ij = e4m3(J32_ij / s_i), s_i = max_j |J32_ij| / 448 (1 for a zero row).
 cudaError_t launch_prepare_J8(const float* J32, int Np, unsigned char* J8, float* scale, cudaStream_t s);
@@ -113,6 +115,8 @@ cudaError_t launch_gdmod_step(const StepArgs& a, const float* J, float* K, const
 cudaError_t launch_to_e4m3(const float* x, unsigned char* y, size_t n, cudaStream_t s);
 int tc_mtiles(int N);
 int tc_pick_bn(int N, int C);
+int tc_pick_bn_pair(int N, int C);
+bool tc_pair_pays(int N, int C);
 bool tc_supported(int device);
 
 }  // namespace gda

@@ -6,6 +6,32 @@ namespace gda {
 
 int tc_mtiles(int N) { return (N + BM - 1) / BM; }
 
+// Two-SM pairs: a 256 x BN pair tile costs each SM about max(BN, 128 + BN / 2)
+// cycles per 16-deep K slice (MMA time against its shared-memory feed: own A
+// rows plus half of B), over ceil(pair tiles / clusters) rounds.
+int tc_pick_bn_pair(int N, int C) {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 2) sms = 148;
+  }
+  const int clusters = sms / 2;
+  const int widths[3] = {128, 224, 256};
+  int best = 128;
+  long long best_cost = -1;
+  for (int bn : widths) {
+    const long long ptiles = (long long)((C + bn - 1) / bn) * (((N + BM - 1) / BM) / 2);
+    const long long per = bn > 128 + bn / 2 ? bn : 128 + bn / 2;
+    const long long cost = ((ptiles + clusters - 1) / clusters) * per;
+    if (best_cost < 0 || cost < best_cost) {
+      best_cost = cost;
+      best = bn;
+    }
+  }
+  return best;
+}
+
 // Tile width for N spins and C columns: the busiest CTA runs ceil(tiles / SMs)
 // tiles, and a 128 x BN tile costs about (128 + BN) shared-memory cycles per
 // K-slice of 16 (MMA reads plus TMA writes of A and B at ~128 B/clk), so pick
@@ -31,6 +57,20 @@ int tc_pick_bn(int N, int C) {
   return best;
 }
 
+// AUTO's choice: two-SM tiles when the row blocks pair up and the pair tiles
+// fill at least three waves of clusters (measured on GB300: 5-10 % faster at
+// N = R = 4096 and above, 5-15 % slower on one or two waves).
+bool tc_pair_pays(int N, int C) {
+  const int mt = (N + BM - 1) / BM;
+  if (mt % 2) return false;
+  int sms = 0, dev = 0;
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 2) return false;
+  const int bn = tc_pick_bn_pair(N, C);
+  const long long ptiles = (long long)((C + bn - 1) / bn) * (mt / 2);
+  return ptiles >= 3LL * (sms / 2);
+}
+
 bool tc_supported(int device) {
   int major = 0, minor = 0;
   if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, device) != cudaSuccess) return false;
@@ -41,9 +81,7 @@ bool tc_supported(int device) {
 cudaError_t tc_plan_create(TcPlan** plan, const __nv_bfloat16* J16, int Np, const __nv_bfloat16* ops, int n_op_bufs,
                            int Cp) {
   TcPlan* p = new TcPlan();
-  p->Cp = Cp;
-  if (!make_map(&p->A, J16, Np, Np, BM) || !make_map(&p->B128, ops, Np, n_op_bufs * Cp, 128) ||
-      !make_map(&p->B224, ops, Np, n_op_bufs * Cp, 224) || !make_map(&p->B256, ops, Np, n_op_bufs * Cp, 256)) {
+  if (!plan_maps<false>(p, J16, Np, ops, n_op_bufs, Cp)) {
     delete p;
     return cudaErrorInvalidValue;
   }
@@ -56,12 +94,8 @@ void tc_plan_destroy(TcPlan* plan) { delete plan; }
 const CUtensorMap* tc_plan_A(const TcPlan* plan) { return &plan->A; }
 const CUtensorMap* tc_plan_B(const TcPlan* plan) { return &plan->B128; }
 
-cudaError_t launch_step_tc(const TcPlan* plan, const StepArgs& a, int op_buf, cudaStream_t s) {
-  const int b_row0 = op_buf * plan->Cp;
-  const int bn = tc_pick_bn(a.N, a.C);
-  if (bn == 256) return dispatch_mode<256, 4, false>(plan->A, plan->B256, b_row0, a, s);
-  if (bn == 224) return dispatch_mode<224, 4, false>(plan->A, plan->B224, b_row0, a, s);
-  return dispatch_mode<128, 6, false>(plan->A, plan->B128, b_row0, a, s);
+cudaError_t launch_step_tc(const TcPlan* plan, const StepArgs& a, int op_buf, cudaStream_t s, bool pair) {
+  return launch_plan<false>(plan, a, op_buf, pair, s);
 }
 
 }  // namespace gda

@@ -37,10 +37,13 @@ struct TcThreads {
   static constexpr int N = 64 + 32 * EPI;
 };
 
-template <int BN, int STAGES>
+// PAIR: two-SM tiles (cta_group::2); each CTA of the pair stages its own 128
+// rows of A and half (BN / 2) of B's columns.
+template <int BN, int STAGES, bool PAIR = false>
 struct TcCfg {
+  static constexpr int BH = PAIR ? BN / 2 : BN;  // B columns staged per CTA
   static constexpr uint32_t A_BYTES = BM * BK * 2;
-  static constexpr uint32_t B_BYTES = BN * BK * 2;
+  static constexpr uint32_t B_BYTES = BH * BK * 2;
   static constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
   static constexpr uint32_t TAIL = (2 * STAGES + 4) * 8 + 6 * BN * 4 + 16;
   static constexpr uint32_t SMEM = 1024 + STAGES * STAGE_BYTES + TAIL;
@@ -49,11 +52,19 @@ struct TcCfg {
 // Persistent over output tiles: CTA b processes tiles b, b + gridDim.x, ...
 // (column block fastest), with two tensor-memory accumulators so that the
 // epilogue of one tile overlaps the MMAs of the next.
-template <int BN, int STAGES, bool CPLX, int MODE, bool F8>
+//
+// PAIR: launched in clusters of two CTAs; cluster c processes pair tiles c,
+// c + clusters, ... of 256 x BN (row blocks 2p and 2p + 1, one per CTA).
+// Both CTAs load their A rows and their half of B with completion counted on
+// the even CTA's full barrier; the even CTA's MMA warp issues M = 256 MMAs and
+// commits to the empty / accumulator barriers of both CTAs; each CTA's
+// epilogue reads its own 128 accumulator rows and arrives on the even CTA's
+// accumulator-empty barrier.
+template <int BN, int STAGES, bool CPLX, int MODE, bool F8, bool PAIR>
 __global__ void __launch_bounds__(TcThreads<MODE>::N, 1)
     step_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int b_row0,
                    StepArgs a) {
-  using Cfg = TcCfg<BN, STAGES>;
+  using Cfg = TcCfg<BN, STAGES, PAIR>;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
@@ -71,7 +82,13 @@ __global__ void __launch_bounds__(TcThreads<MODE>::N, 1)
   constexpr int BKE = F8 ? 2 * BK : BK;  // elements per 128-byte K slice
   const int KB = (a.N + BKE - 1) / BKE;
   const int NT = (a.C + BN - 1) / BN;
-  const int T = NT * ((a.N + BM - 1) / BM);
+  const int MT = (a.N + BM - 1) / BM;  // even when PAIR (the host checks)
+  const int T = NT * (PAIR ? MT / 2 : MT);
+  const uint32_t rank = PAIR ? cluster_ctarank() : 0u;
+  const bool leader = rank == 0;
+  const int unit0 = PAIR ? int(cluster_id_x()) : int(blockIdx.x);
+  const int nunit = PAIR ? int(ncluster_x()) : int(gridDim.x);
+  auto tile_m0 = [&](int t) { return (PAIR ? 2 * (t / NT) + int(rank) : t / NT) * BM; };
   auto full_bar = [&](int s) { return smem_u32(bars + s); };
   auto empty_bar = [&](int s) { return smem_u32(bars + STAGES + s); };
   auto acc_full = [&](int b) { return smem_u32(bars + 2 * STAGES + b); };
@@ -85,16 +102,22 @@ __global__ void __launch_bounds__(TcThreads<MODE>::N, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(acc_full(b), 1);
-      mbar_init(acc_empty(b), 1);
+      mbar_init(acc_empty(b), PAIR ? 2 : 1);
     }
     s_flag[0] = 0;
     s_flag[1] = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   constexpr uint32_t TCOLS = 2 * BN <= 256 ? 256 : 512;  // power of two
-  if (warp == 1) tmem_alloc(smem_u32(s_tmem), TCOLS);
+  if (warp == 1) {
+    if (PAIR)
+      tmem_alloc_pair(smem_u32(s_tmem), TCOLS);
+    else
+      tmem_alloc(smem_u32(s_tmem), TCOLS);
+  }
   tc_fence_before();
   __syncthreads();
+  if (PAIR) cluster_sync();  // barriers of both CTAs initialised before any remote arrival
   tc_fence_after();
   const uint32_t tmem = *s_tmem;
   if (threadIdx.x == 0) stamp(a, 1);
@@ -104,8 +127,8 @@ __global__ void __launch_bounds__(TcThreads<MODE>::N, 1)
     if (lane == 0) {
       int it = 0;
       bool stop = false;
-      for (int t = blockIdx.x; t < T && !stop; t += gridDim.x) {
-        const int m0 = (t / NT) * BM, n0 = (t % NT) * BN;
+      for (int t = unit0; t < T && !stop; t += nunit) {
+        const int m0 = tile_m0(t), n0 = (t % NT) * BN + int(rank) * Cfg::BH;
         for (int kb = 0; kb < KB; ++kb, ++it) {
           const int s = it % STAGES;
           const uint32_t ph = (it / STAGES) & 1;
@@ -113,26 +136,43 @@ __global__ void __launch_bounds__(TcThreads<MODE>::N, 1)
             stop = true;
             break;
           }
-          mbar_arrive_expect_tx(full_bar(s), Cfg::STAGE_BYTES);
-          tma_load_2d(sA + s * Cfg::A_BYTES, &tmA, kb * BKE, m0, full_bar(s));
-          tma_load_2d(sB + s * Cfg::B_BYTES, &tmB, kb * BKE, b_row0 + n0, full_bar(s));
+          if (PAIR) {
+            const uint32_t fb = mapa_shared(full_bar(s), 0);  // the even CTA counts both CTAs' bytes
+            if (leader) mbar_arrive_expect_tx(full_bar(s), 2 * Cfg::STAGE_BYTES);
+            tma_load_2d_pair(sA + s * Cfg::A_BYTES, &tmA, kb * BKE, m0, fb);
+            tma_load_2d_pair(sB + s * Cfg::B_BYTES, &tmB, kb * BKE, b_row0 + n0, fb);
+          } else {
+            mbar_arrive_expect_tx(full_bar(s), Cfg::STAGE_BYTES);
+            tma_load_2d(sA + s * Cfg::A_BYTES, &tmA, kb * BKE, m0, full_bar(s));
+            tma_load_2d(sB + s * Cfg::B_BYTES, &tmB, kb * BKE, b_row0 + n0, full_bar(s));
+          }
         }
       }
       if (stop) {
         atomicOr(&s_flag[0], 1);
-        for (int k = it - 1; k >= 0 && k >= it - STAGES; --k) (void)mbar_wait(full_bar(k % STAGES), (k / STAGES) & 1);
+        // copies still in flight: the even CTA waits for its full barriers (they
+        // count both CTAs' bytes); the odd CTA for the MMAs that consume its
+        // stages to release them (bounded: the even CTA may have stopped)
+        for (int k = it - 1; k >= 0 && k >= it - STAGES; --k) {
+          if (!PAIR || leader)
+            (void)mbar_wait(full_bar(k % STAGES), (k / STAGES) & 1);
+          else
+            (void)mbar_wait(empty_bar(k % STAGES), (k / STAGES) & 1);
+        }
       }
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
-    if (lane == 0) {
-      constexpr uint32_t idesc = F8 ? idesc_e4m3<BN>() : idesc_bf16<BN>();
+    if (lane == 0 && leader) {
+      constexpr uint32_t idesc = PAIR ? (F8 ? idesc_e4m3_m256<BN>() : idesc_bf16_m256<BN>())
+                                      : (F8 ? idesc_e4m3<BN>() : idesc_bf16<BN>());
       int it = 0, lt = 0;
       bool stop = false;
-      for (int t = blockIdx.x; t < T && !stop; t += gridDim.x, ++lt) {
+      for (int t = unit0; t < T && !stop; t += nunit, ++lt) {
         const int b = lt & 1;
         const uint32_t use = lt >> 1;
-        if (!mbar_wait(acc_empty(b), (use & 1) ^ 1u) || *(volatile int*)&s_flag[0]) {
+        const bool free_ok = PAIR ? mbar_wait_cluster(acc_empty(b), (use & 1) ^ 1u) : mbar_wait(acc_empty(b), (use & 1) ^ 1u);
+        if (!free_ok || *(volatile int*)&s_flag[0]) {
           stop = true;
           break;
         }
@@ -151,15 +191,28 @@ __global__ void __launch_bounds__(TcThreads<MODE>::N, 1)
           for (int k = 0; k < 4; ++k) {  // 32 bytes of K per instruction
             const uint64_t da = sdesc_sw128(sA + s * Cfg::A_BYTES + k * 32);
             const uint64_t db = sdesc_sw128(sB + s * Cfg::B_BYTES + k * 32);
-            if (F8)
-              mma_e4m3(dacc, da, db, idesc, (kb | k) != 0);
-            else
-              mma_bf16(dacc, da, db, idesc, (kb | k) != 0);
+            if (PAIR) {
+              if (F8)
+                mma_e4m3_pair(dacc, da, db, idesc, (kb | k) != 0);
+              else
+                mma_bf16_pair(dacc, da, db, idesc, (kb | k) != 0);
+            } else {
+              if (F8)
+                mma_e4m3(dacc, da, db, idesc, (kb | k) != 0);
+              else
+                mma_bf16(dacc, da, db, idesc, (kb | k) != 0);
+            }
           }
-          mma_commit(empty_bar(s));
+          if (PAIR)
+            mma_commit_pair(empty_bar(s));
+          else
+            mma_commit(empty_bar(s));
         }
         if (lt == 0) stamp(a, 3);
-        mma_commit(acc_full(b));  // also after an abort: tracks every MMA issued into b
+        if (PAIR)
+          mma_commit_pair(acc_full(b));  // also after an abort: tracks every MMA issued into b
+        else
+          mma_commit(acc_full(b));
         if (stop) {
           (void)mbar_wait(acc_full(b), use & 1);  // those MMAs finish before the CTA frees TMEM
           break;
@@ -185,9 +238,9 @@ __global__ void __launch_bounds__(TcThreads<MODE>::N, 1)
     int bad = 0;
     int lt = 0;
     EpiRegs<MODE, CPLX, CW> R[2];
-    for (int t = blockIdx.x; t < T; t += gridDim.x, ++lt) {
-      const int mt = t / NT;
-      const int m0 = mt * BM, n0 = (t % NT) * BN;
+    for (int t = unit0; t < T; t += nunit, ++lt) {
+      const int m0 = tile_m0(t), n0 = (t % NT) * BN;
+      const int mt = m0 / BM;
       const int b = lt & 1;
       const uint32_t use = lt >> 1;
       const int rbase = n0 / W;
@@ -242,7 +295,12 @@ __global__ void __launch_bounds__(TcThreads<MODE>::N, 1)
       if (NCH & 1) body(NCH - 1, R[0], R[1]);
       tc_fence_before();
       epi_bar_sync_n<32 * NEPI>();
-      if (e == 0) mbar_arrive(acc_empty(b));  // accumulator b may be overwritten
+      if (e == 0) {  // accumulator b may be overwritten
+        if (PAIR && !leader)
+          mbar_arrive_cluster(mapa_shared(acc_empty(b), 0));
+        else
+          mbar_arrive(acc_empty(b));
+      }
       if (lt == 0 && e == 0) stamp(a, 5);
       if (e < RPT) {
         const int r = rbase + e;
@@ -261,11 +319,15 @@ __global__ void __launch_bounds__(TcThreads<MODE>::N, 1)
 
   tc_fence_before();
   __syncthreads();
+  if (PAIR) cluster_sync();  // no CTA leaves while its peer may still signal or read it
   if (threadIdx.x == 0 && s_flag[0]) atomicOr(a.err, E_TIMEOUT);
   if (threadIdx.x == 0) stamp(a, 7);
   if (warp == 1) {
     tc_fence_after();
-    tmem_dealloc(tmem, TCOLS);
+    if (PAIR)
+      tmem_dealloc_pair(tmem, TCOLS);
+    else
+      tmem_dealloc(tmem, TCOLS);
   }
 }
 
@@ -302,11 +364,11 @@ bool make_map(CUtensorMap* m, const void* ptr, int Np, int rows, int box_rows, b
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int BN, int STAGES, bool CPLX, int MODE, bool F8>
+template <int BN, int STAGES, bool CPLX, int MODE, bool F8, bool PAIR>
 cudaError_t launch_cfg(const CUtensorMap& A, const CUtensorMap& B, int b_row0, const StepArgs& a, cudaStream_t s) {
-  using Cfg = TcCfg<BN, STAGES>;
+  using Cfg = TcCfg<BN, STAGES, PAIR>;
   static bool attr_set = false;
-  auto kern = step_tc_kernel<BN, STAGES, CPLX, MODE, F8>;
+  auto kern = step_tc_kernel<BN, STAGES, CPLX, MODE, F8, PAIR>;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
     if (e != cudaSuccess) return e;
@@ -318,29 +380,54 @@ cudaError_t launch_cfg(const CUtensorMap& A, const CUtensorMap& B, int b_row0, c
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return cudaErrorUnknown;
   }
-  const int tiles = ((a.C + BN - 1) / BN) * ((a.N + BM - 1) / BM);
-  kern<<<tiles < sms ? tiles : sms, TcThreads<MODE>::N, Cfg::SMEM, s>>>(A, B, b_row0, a);
-  return cudaGetLastError();
+  const int NT = (a.C + BN - 1) / BN, MT = (a.N + BM - 1) / BM;
+  if (!PAIR) {
+    const int tiles = NT * MT;
+    kern<<<tiles < sms ? tiles : sms, TcThreads<MODE>::N, Cfg::SMEM, s>>>(A, B, b_row0, a);
+    return cudaGetLastError();
+  }
+  if (MT % 2) return cudaErrorInvalidValue;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.blockDim = dim3(TcThreads<MODE>::N);
+  cfg.dynamicSmemBytes = Cfg::SMEM;
+  cfg.stream = s;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  static int max_clusters = 0;
+  if (!max_clusters) {
+    cfg.gridDim = dim3(2 * (sms / 2));
+    cudaError_t e = cudaOccupancyMaxActiveClusters(&max_clusters, kern, &cfg);
+    if (e != cudaSuccess) return e;
+    if (max_clusters < 1) return cudaErrorLaunchOutOfResources;
+  }
+  const int ptiles = NT * (MT / 2);
+  cfg.gridDim = dim3(2 * (ptiles < max_clusters ? ptiles : max_clusters));
+  return cudaLaunchKernelEx(&cfg, kern, A, B, b_row0, a);
 }
 
-template <int BN, int STAGES, bool CPLX, bool F8>
+template <int BN, int STAGES, bool CPLX, bool F8, bool PAIR>
 cudaError_t dispatch_cplx(const CUtensorMap& A, const CUtensorMap& B, int b_row0, const StepArgs& a, cudaStream_t s) {
   switch (a.mode) {
-    case M_EULER: return launch_cfg<BN, STAGES, CPLX, M_EULER, F8>(A, B, b_row0, a, s);
-    case M_RK1: return launch_cfg<BN, STAGES, CPLX, M_RK1, F8>(A, B, b_row0, a, s);
-    case M_RK2: return launch_cfg<BN, STAGES, CPLX, M_RK2, F8>(A, B, b_row0, a, s);
-    case M_RK3: return launch_cfg<BN, STAGES, CPLX, M_RK3, F8>(A, B, b_row0, a, s);
-    case M_RK4: return launch_cfg<BN, STAGES, CPLX, M_RK4, F8>(A, B, b_row0, a, s);
-    case M_ENERGY: return launch_cfg<BN, STAGES, CPLX, M_ENERGY, F8>(A, B, b_row0, a, s);
-    case M_RAW: return launch_cfg<BN, STAGES, CPLX, M_RAW, F8>(A, B, b_row0, a, s);
+    case M_EULER: return launch_cfg<BN, STAGES, CPLX, M_EULER, F8, PAIR>(A, B, b_row0, a, s);
+    case M_RK1: return launch_cfg<BN, STAGES, CPLX, M_RK1, F8, PAIR>(A, B, b_row0, a, s);
+    case M_RK2: return launch_cfg<BN, STAGES, CPLX, M_RK2, F8, PAIR>(A, B, b_row0, a, s);
+    case M_RK3: return launch_cfg<BN, STAGES, CPLX, M_RK3, F8, PAIR>(A, B, b_row0, a, s);
+    case M_RK4: return launch_cfg<BN, STAGES, CPLX, M_RK4, F8, PAIR>(A, B, b_row0, a, s);
+    case M_ENERGY: return launch_cfg<BN, STAGES, CPLX, M_ENERGY, F8, PAIR>(A, B, b_row0, a, s);
+    case M_RAW: return launch_cfg<BN, STAGES, CPLX, M_RAW, F8, PAIR>(A, B, b_row0, a, s);
   }
   return cudaErrorInvalidValue;
 }
 
-template <int BN, int STAGES, bool F8>
+template <int BN, int STAGES, bool F8, bool PAIR = false>
 cudaError_t dispatch_mode(const CUtensorMap& A, const CUtensorMap& B, int b_row0, const StepArgs& a, cudaStream_t s) {
-  return a.cplx ? dispatch_cplx<BN, STAGES, true, F8>(A, B, b_row0, a, s)
-                : dispatch_cplx<BN, STAGES, false, F8>(A, B, b_row0, a, s);
+  return a.cplx ? dispatch_cplx<BN, STAGES, true, F8, PAIR>(A, B, b_row0, a, s)
+                : dispatch_cplx<BN, STAGES, false, F8, PAIR>(A, B, b_row0, a, s);
 }
 
 }  // namespace
@@ -350,7 +437,35 @@ struct TcPlan {  // tensor maps of one operand set (BF16 or FP8)
   CUtensorMap B128;
   CUtensorMap B224;
   CUtensorMap B256;
+  CUtensorMap B64;   // halves of 128- and 224-wide tiles for two-SM pairs
+  CUtensorMap B112;
   int Cp;
 };
+
+// Shared by both precisions: the tensor maps of an operand set, then the
+// launch for the tile width the chooser picks.
+template <bool F8>
+bool plan_maps(TcPlan* p, const void* Jop, int Np, const void* ops, int n_op_bufs, int Cp) {
+  p->Cp = Cp;
+  const int rows = n_op_bufs * Cp;
+  return make_map(&p->A, Jop, Np, Np, BM, F8) && make_map(&p->B128, ops, Np, rows, 128, F8) &&
+         make_map(&p->B224, ops, Np, rows, 224, F8) && make_map(&p->B256, ops, Np, rows, 256, F8) &&
+         make_map(&p->B64, ops, Np, rows, 64, F8) && make_map(&p->B112, ops, Np, rows, 112, F8);
+}
+
+template <bool F8>
+cudaError_t launch_plan(const TcPlan* plan, const StepArgs& a, int op_buf, bool pair, cudaStream_t s) {
+  const int b_row0 = op_buf * plan->Cp;
+  if (pair) {
+    const int bn = tc_pick_bn_pair(a.N, a.C);
+    if (bn == 256) return dispatch_mode<256, 6, F8, true>(plan->A, plan->B128, b_row0, a, s);
+    if (bn == 224) return dispatch_mode<224, 6, F8, true>(plan->A, plan->B112, b_row0, a, s);
+    return dispatch_mode<128, 8, F8, true>(plan->A, plan->B64, b_row0, a, s);
+  }
+  const int bn = tc_pick_bn(a.N, a.C);
+  if (bn == 256) return dispatch_mode<256, 4, F8>(plan->A, plan->B256, b_row0, a, s);
+  if (bn == 224) return dispatch_mode<224, 4, F8>(plan->A, plan->B224, b_row0, a, s);
+  return dispatch_mode<128, 6, F8>(plan->A, plan->B128, b_row0, a, s);
+}
 
 }  // namespace gda

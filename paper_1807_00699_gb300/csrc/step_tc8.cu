@@ -61,10 +61,7 @@ cudaError_t launch_to_e4m3(const float* x, unsigned char* y, size_t n, cudaStrea
 cudaError_t tc_plan8_create(TcPlan** plan, const unsigned char* J8, int Np, const unsigned char* ops8, int n_op_bufs,
                             int Cp) {
   TcPlan* p = new TcPlan();
-  p->Cp = Cp;
-  if (!make_map(&p->A, J8, Np, Np, BM, true) || !make_map(&p->B128, ops8, Np, n_op_bufs * Cp, 128, true) ||
-      !make_map(&p->B224, ops8, Np, n_op_bufs * Cp, 224, true) ||
-      !make_map(&p->B256, ops8, Np, n_op_bufs * Cp, 256, true)) {
+  if (!plan_maps<true>(p, J8, Np, ops8, n_op_bufs, Cp)) {
     delete p;
     return cudaErrorInvalidValue;
   }
@@ -72,13 +69,9 @@ cudaError_t tc_plan8_create(TcPlan** plan, const unsigned char* J8, int Np, cons
   return cudaSuccess;
 }
 
-cudaError_t launch_step_tc8(const TcPlan* plan, const StepArgs& a, int op_buf, cudaStream_t s) {
+cudaError_t launch_step_tc8(const TcPlan* plan, const StepArgs& a, int op_buf, cudaStream_t s, bool pair) {
   if (!a.row_scale) return cudaErrorInvalidValue;
-  const int b_row0 = op_buf * plan->Cp;
-  const int bn = tc_pick_bn(a.N, a.C);
-  if (bn == 256) return dispatch_mode<256, 4, true>(plan->A, plan->B256, b_row0, a, s);
-  if (bn == 224) return dispatch_mode<224, 4, true>(plan->A, plan->B224, b_row0, a, s);
-  return dispatch_mode<128, 6, true>(plan->A, plan->B128, b_row0, a, s);
+  return launch_plan<true>(plan, a, op_buf, pair, s);
 }
 
 }  // namespace gda
