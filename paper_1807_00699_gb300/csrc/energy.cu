@@ -480,3 +480,230 @@ cudaError_t launch_prepare_J(const double* J64, int Np, float* J32, __nv_bfloat1
 }
 
 }  // namespace gda
+
+// ---------------------------------------------------------------- ranking
+// Candidate ranking for the argmin of the FP64 energies (gda_best): every
+// restart's Eq. (1) energy is first bounded in FP32 with compensated sums,
+// then only the restarts within twice the error bound of the lowest such
+// value are evaluated in FP64.  The FP64 argmin over those candidates is the
+// FP64 argmin over all restarts (ties: lowest index, candidates ascending).
+namespace gda {
+namespace {
+
+// FP32 projection computed in double, rounded once (|s32 - s| <= 2^-24 |s|).
+__global__ void k_project_rank(const float* psi, float* S, int N, int Np, int R, int cplx) {
+  const size_t total = size_t(R) * N;
+  for (size_t idx = blockIdx.x * size_t(blockDim.x) + threadIdx.x; idx < total; idx += size_t(gridDim.x) * blockDim.x) {
+    const int r = int(idx / N), i = int(idx % N);
+    if (cplx) {
+      const double re = psi[size_t(2 * r) * Np + i], im = psi[size_t(2 * r + 1) * Np + i];
+      const double m = sqrt(re * re + im * im);
+      S[size_t(2 * r) * Np + i] = float(m > 0.0 ? re / m : 1.0);
+      S[size_t(2 * r + 1) * Np + i] = float(m > 0.0 ? im / m : 0.0);
+    } else {
+      S[size_t(r) * Np + i] = psi[size_t(r) * Np + i] >= 0.0f ? 1.0f : -1.0f;
+    }
+  }
+}
+
+// T = J0 S over 64 x 64 tiles (4 x 4 per thread) in FP32: each 16-deep K
+// block is summed with FMAs, then added into a (hi, lo) pair with an exact
+// two-sum, so one element's error is at most ~17 u sum_j |J0_ij S_j|.  The
+// Eq. (1) partials per tile of 64 rows are formed and summed in double.
+template <bool CPLX>
+__global__ void __launch_bounds__(256) k_energy32c(const float* __restrict__ J, const float* __restrict__ S,
+                                                   const double* __restrict__ g, int N, int Np, int R, int Rp,
+                                                   double* part) {
+  constexpr int BM = 64, BN = 64, BK = 16;
+  __shared__ float As[BK][BM + 1];
+  __shared__ float Bs[BK][BN + 1];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  float hi[4][4], lo[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) hi[a][b] = lo[a][b] = 0.0f;
+  const int lr = tid >> 2, lk = (tid & 3) * 4;
+  for (int k0 = 0; k0 < Np; k0 += BK) {
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      As[lk + t][lr] = J[size_t(m0 + lr) * Np + k0 + lk + t];
+      Bs[lk + t][lr] = S[size_t(n0 + lr) * Np + k0 + lk + t];
+    }
+    __syncthreads();
+    float blk[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) blk[a][b] = 0.0f;
+#pragma unroll
+    for (int k = 0; k < BK; ++k) {
+      float b[4];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) b[v] = Bs[k][4 * ty + v];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const float av = As[k][tx + 16 * a];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) blk[a][v] = __fmaf_rn(av, b[v], blk[a][v]);
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {  // two-sum (Knuth): hi + blk = s + e exactly
+        const float s = __fadd_rn(hi[a][v], blk[a][v]);
+        const float bp = __fsub_rn(s, hi[a][v]);
+        const float e = __fadd_rn(__fsub_rn(hi[a][v], __fsub_rn(s, bp)), __fsub_rn(blk[a][v], bp));
+        hi[a][v] = s;
+        lo[a][v] = __fadd_rn(lo[a][v], e);
+      }
+  }
+  constexpr int U = CPLX ? 2 : 4;
+  double rs[4] = {0.0, 0.0, 0.0, 0.0};
+  const int c0 = n0 + 4 * ty;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int i = m0 + tx + 16 * a;
+    if (i >= N) continue;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (CPLX) {
+        const int c = c0 + 2 * u;
+        const double sr = S[size_t(c) * Np + i], si = S[size_t(c + 1) * Np + i];
+        const double tr = double(hi[a][2 * u]) + double(lo[a][2 * u]);
+        const double ti = double(hi[a][2 * u + 1]) + double(lo[a][2 * u + 1]);
+        rs[u] += -(sr * tr + si * ti) + g[i] * sr;
+      } else {
+        const int c = c0 + u;
+        const double sv = S[size_t(c) * Np + i];
+        rs[u] += -sv * (double(hi[a][u]) + double(lo[a][u])) + g[i] * sv;
+      }
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < U; ++u)
+#pragma unroll
+    for (int off = 8; off; off >>= 1) rs[u] += __shfl_xor_sync(0xffffffffu, rs[u], off);
+  if (tx == 0) {
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int r = (CPLX ? c0 / 2 : c0) + u;
+      if (r < R) part[size_t(blockIdx.y) * Rp + r] = rs[u];
+    }
+  }
+}
+
+// sum_ij |J0_ij| + sum_i |g_i| (J0: the FP64 J without its diagonal).
+__global__ void k_abs_sum(const double* J64, const double* g, int N, int Np, double* out) {
+  double s = 0.0;
+  for (size_t idx = blockIdx.x * size_t(blockDim.x) + threadIdx.x; idx < size_t(N) * N;
+       idx += size_t(gridDim.x) * blockDim.x) {
+    const int i = int(idx / N), j = int(idx % N);
+    if (i != j) s += fabs(J64[size_t(i) * Np + j]);
+    if (j == 0 && g) s += fabs(g[i]);
+  }
+  for (int off = 16; off; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if ((threadIdx.x & 31) == 0) atomicAdd(out, s);
+}
+
+// One block: E32[r] = sum_t part[t][r] + diag; the restarts with E32 <= min + margin,
+// ascending, to idx[0 .. *count).
+__global__ void k_rank(const double* part, int mt, int R, int Rp, double diag, double margin, double* E32, int* idx,
+                       int* count) {
+  __shared__ double smin[32];
+  __shared__ int spre[1024 / 32 + 1];
+  __shared__ int sbase;
+  double mn = DBL_MAX;
+  for (int r = threadIdx.x; r < R; r += blockDim.x) {
+    double s = 0.0;
+    for (int t = 0; t < mt; ++t) s += part[size_t(t) * Rp + r];
+    s += diag;
+    E32[r] = s;
+    mn = fmin(mn, s);
+  }
+  for (int off = 16; off; off >>= 1) mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, off));
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  if (lane == 0) smin[w] = mn;
+  if (threadIdx.x == 0) sbase = 0;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 1; k < nw; ++k) mn = fmin(mn, smin[k]);
+    smin[0] = mn;
+  }
+  __syncthreads();
+  const double lim = smin[0] + margin;
+  for (int r0 = 0; r0 < R; r0 += blockDim.x) {
+    const int r = r0 + threadIdx.x;
+    const bool in = r < R && E32[r] <= lim;
+    const unsigned m = __ballot_sync(0xffffffffu, in);
+    if (lane == 0) spre[w] = __popc(m);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int acc = sbase;
+      for (int k = 0; k < nw; ++k) {
+        const int c = spre[k];
+        spre[k] = acc;
+        acc += c;
+      }
+      spre[nw] = acc;
+    }
+    __syncthreads();
+    if (in) idx[spre[w] + __popc(m & ((1u << lane) - 1u))] = r;
+    __syncthreads();
+    if (threadIdx.x == 0) sbase = spre[nw];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *count = sbase;
+}
+
+// Candidate columns (restart idx[k] -> column block k) of psi into a compact buffer.
+__global__ void k_gather_cols(const float* psi, int Np, const int* idx, int count, int cplx, float* out) {
+  const int W = cplx ? 2 : 1;
+  const size_t total = size_t(count) * W * Np;
+  for (size_t q = blockIdx.x * size_t(blockDim.x) + threadIdx.x; q < total; q += size_t(gridDim.x) * blockDim.x) {
+    const int col = int(q / Np), i = int(q % Np);
+    const int k = col / W, w = col % W;
+    out[q] = psi[size_t(idx[k] * W + w) * Np + i];
+  }
+}
+
+__global__ void k_map_best(const int* idx, int* bestR) { *bestR = idx[*bestR]; }
+
+}  // namespace
+
+cudaError_t launch_abs_sum(const double* J64, const double* g, int N, int Np, double* out, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double), s);
+  if (e != cudaSuccess) return e;
+  k_abs_sum<<<grid_for(size_t(N) * N), 256, 0, s>>>(J64, g, N, Np, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rank(const float* psi, const float* J32, const double* g, float* S32, double* part, double* E32,
+                        int* idx, int* count, int N, int Np, int R, int Rp, int C, int cplx, double diag,
+                        double margin, cudaStream_t s) {
+  k_project_rank<<<grid_for(size_t(R) * N), 256, 0, s>>>(psi, S32, N, Np, R, cplx);
+  const int mt = (N + 63) / 64;
+  dim3 grid((C + 63) / 64, mt);
+  if (cplx)
+    k_energy32c<true><<<grid, 256, 0, s>>>(J32, S32, g, N, Np, R, Rp, part);
+  else
+    k_energy32c<false><<<grid, 256, 0, s>>>(J32, S32, g, N, Np, R, Rp, part);
+  k_rank<<<1, 1024, 0, s>>>(part, mt, R, Rp, diag, margin, E32, idx, count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_cols(const float* psi, int Np, const int* idx, int count, int cplx, float* out,
+                               cudaStream_t s) {
+  k_gather_cols<<<grid_for(size_t(count) * (cplx ? 2 : 1) * Np), 256, 0, s>>>(psi, Np, idx, count, cplx, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_map_best(const int* idx, int* bestR, cudaStream_t s) {
+  k_map_best<<<1, 1, 0, s>>>(idx, bestR);
+  return cudaGetLastError();
+}
+
+}  // namespace gda

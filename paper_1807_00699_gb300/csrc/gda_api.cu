@@ -79,6 +79,12 @@ struct gda_ctx {
   double* E64 = nullptr;
   double* bestE = nullptr;
   int* bestR = nullptr;
+  double* E32 = nullptr;    // ranking: compensated FP32 energies [rank_cap]
+  int* cidx = nullptr;      // ranking: candidate restarts [rank_cap]
+  int* d_count = nullptr;
+  double* d_abs = nullptr;
+  int rank_cap = 0;
+  double abs_sum = -1.0;    // sum |J0| + sum |g| of the current instance (-1: not computed)
   signed char* cfg8 = nullptr;
   double* cfgth = nullptr;
   long long* t_step = nullptr;
@@ -224,6 +230,7 @@ gda_status load_instance(gda_ctx* c, const double* J, const double* g, cudaMemcp
   if (g) CK(cudaMemcpyAsync(c->g64, g, N * sizeof(double), kind, c->stream));
   c->K_R = 0;  // a GD-mod coupling state belongs to the previous J
   c->ell_maxdeg = -1;
+  c->abs_sum = -1.0;
   CK(cudaMemsetAsync(c->d_flags, 0, sizeof(int), c->stream));
   CK(cudaMemsetAsync(c->d_maxabs, 0, sizeof(unsigned long long), c->stream));
   LK(launch_check_instance(c->J64, c->g64, c->N, c->Np, c->d_flags, c->d_maxabs, c->d_diag, c->stream));
@@ -500,6 +507,7 @@ void gda_destroy(gda_ctx* c) {
   dfree(c->J64); dfree(c->J32); dfree(c->J16); dfree(c->J8); dfree(c->jscale); dfree(c->Jint); dfree(c->g64); dfree(c->g32); dfree(c->h1);
   dfree(c->d_flags); dfree(c->d_maxabs); dfree(c->d_diag);
   dfree(c->bestE); dfree(c->bestR); dfree(c->cfg8); dfree(c->cfgth);
+  dfree(c->E32); dfree(c->cidx); dfree(c->d_count); dfree(c->d_abs);
   dfree(c->t_step); dfree(c->t_E); dfree(c->t_r); dfree(c->t_count); dfree(c->err); dfree(c->flags);
   dfree(c->stamps);
   dfree(c->K);
@@ -765,11 +773,62 @@ gda_status gda_energy(gda_ctx* c, double* E) {
   return check_err(c);
 }
 
+// FP64 argmin through candidate ranking (non-integer energies, R >= 32):
+// compensated FP32 energies of all restarts carry an error below
+// delta = 48 u (sum |J0| + sum |g|) (u = 2^-24: J rounded to FP32, spins
+// rounded once, 16-term FMA blocks plus an exact two-sum, double partials);
+// every restart within 2 (delta + delta64) of the lowest FP32 value is
+// evaluated in FP64 (delta64 covers the FP64 sums themselves), which contains
+// the FP64 argmin over all restarts.  Sets *done = false when ranking does
+// not narrow the set (the caller then evaluates every restart).
+gda_status best_ranked(gda_ctx* c, bool* done) {
+  *done = false;
+  if (c->int_exact || c->R < 32) return GDA_OK;
+  if (c->rank_cap < c->Rp) {
+    dfree(c->E32);
+    dfree(c->cidx);
+    c->rank_cap = 0;
+    CK(dalloc(&c->E32, size_t(c->Rp)));
+    CK(dalloc(&c->cidx, size_t(c->Rp)));
+    c->rank_cap = c->Rp;
+  }
+  if (!c->d_count) CK(dalloc(&c->d_count, 1));
+  if (!c->d_abs) CK(dalloc(&c->d_abs, 1));
+  if (c->abs_sum < 0.0) {
+    LK(launch_abs_sum(c->J64, c->g64, c->N, c->Np, c->d_abs, c->stream));
+    CK(cudaMemcpyAsync(&c->abs_sum, c->d_abs, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  const double u = std::ldexp(1.0, -24);
+  const double delta = 48.0 * u * c->abs_sum;
+  const double delta64 = 1e-9 * (c->abs_sum + std::fabs(c->diag)) + 1e-300;
+  const double margin = 2.0 * (delta + delta64);
+  LK(launch_rank(c->psi[c->cur], c->J32, c->g64, c->S32, c->part64, c->E32, c->cidx, c->d_count, c->N, c->Np, c->R,
+                 c->Rp, c->C, c->cplx, c->diag, margin, c->stream));
+  int count = 0;
+  CK(cudaMemcpyAsync(&count, c->d_count, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (count < 1 || count > c->R / 2) return GDA_OK;
+  LK(launch_gather_cols(c->psi[c->cur], c->Np, c->cidx, count, c->cplx, c->stg[0], c->stream));
+  LK(launch_energy64(c->stg[0], c->J64, c->g64, c->S64, c->part64, c->E64, c->N, c->Np, count, c->Rp,
+                     count * (c->cplx ? 2 : 1), c->cplx, c->stream));
+  LK(launch_argmin(c->E64, count, c->bestE, c->bestR, c->stream));
+  LK(launch_map_best(c->cidx, c->bestR, c->stream));
+  *done = true;
+  return GDA_OK;
+}
+
 gda_status gda_best(gda_ctx* c, double* E, int32_t* r, void* cfg) {
   if (!c) return GDA_ERR_INVALID;
-  gda_status s = compute_energies(c);
+  if (!c->have_state) return fail(c, GDA_ERR_STATE, "no state: call gda_run or gda_set_state first");
+  bool ranked = false;
+  gda_status s = best_ranked(c, &ranked);
   if (s != GDA_OK) return s;
-  LK(launch_argmin(c->E64, c->R, c->bestE, c->bestR, c->stream));
+  if (!ranked) {
+    s = compute_energies(c);
+    if (s != GDA_OK) return s;
+    LK(launch_argmin(c->E64, c->R, c->bestE, c->bestR, c->stream));
+  }
   double e = 0.0;
   int rr = 0;
   CK(cudaMemcpyAsync(&e, c->bestE, sizeof(double), cudaMemcpyDeviceToHost, c->stream));

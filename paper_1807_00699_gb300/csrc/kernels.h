@@ -37,6 +37,17 @@ cudaError_t launch_unpack_state(float* psi, float* gam, float* beta, int N, int 
 cudaError_t launch_check_instance(const double* J64, const double* g, int N, int Np, int* flags,
                                   unsigned long long* maxabs, double* diag, cudaStream_t s);
 cudaError_t launch_prepare_J(const double* J64, int Np, float* J32, __nv_bfloat16* J16, int* Jint, cudaStream_t s);
+// Candidate ranking for the FP64 argmin (energy.cu): *out = sum_ij |J0_ij| + sum |g|;
+// compensated FP32 energies of all restarts into E32 and the restarts within
+// margin of their minimum (ascending) into idx[0 .. *count); candidate columns
+// gathered into a compact buffer; bestR mapped back through idx.
+cudaError_t launch_abs_sum(const double* J64, const double* g, int N, int Np, double* out, cudaStream_t s);
+cudaError_t launch_rank(const float* psi, const float* J32, const double* g, float* S32, double* part, double* E32,
+                        int* idx, int* count, int N, int Np, int R, int Rp, int C, int cplx, double diag,
+                        double margin, cudaStream_t s);
+cudaError_t launch_gather_cols(const float* psi, int Np, const int* idx, int count, int cplx, float* out,
+                               cudaStream_t s);
+cudaError_t launch_map_best(const int* idx, int* bestR, cudaStream_t s);
 cudaError_t launch_features(const double* J, const double* g, int N, int Np, int cplx, double* w0, double* w1,
                             float* F, cudaStream_t s);
 }  // namespace gda

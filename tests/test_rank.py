@@ -1,0 +1,80 @@
+"""gda_best's candidate ranking (compensated FP32 energies bound the FP64 ones;
+only restarts within the bound of the lowest are evaluated in FP64): the
+returned restart and energy equal the argmin of the FP64 energies of all
+restarts (gda_energy), with ties to the lowest index."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gda():
+    import torch
+
+    import __graft_entry__
+    assert torch.cuda.is_available()
+    __graft_entry__.build()
+    from paper_1807_00699_gb300 import gda as mod
+    return mod
+
+
+@pytest.mark.parametrize("model,n,R,steps", [("xy", 1000, 256, 400), ("ising", 777, 300, 300), ("xy", 129, 33, 50)])
+def test_best_equals_full_fp64_argmin(gda, model, n, R, steps):
+    if model == "xy":
+        J, g = synth.xy_gaussian(n, 4)
+    else:
+        J, g = synth.sk_gaussian(n, 4)
+        J, g = J / math.sqrt(n), 0.03 * synth.normal(5, n)
+    J = J.copy()
+    np.fill_diagonal(J, 0.2 * synth.normal(6, n))  # a diagonal shifts every energy
+    s = gda.Solver(J, g, gda.XY if model == "xy" else gda.ISING)
+    s.run(gda.default_params(dt=0.05, eps=0.1, prec=gda.BF16, seed=8), R, steps)
+    E = s.energy()
+    for _ in range(2):  # the second call reuses the cached bound
+        Eb, rb, cfg = s.best()
+        assert rb == int(np.argmin(E)) and Eb == E[rb]
+    psi = s.get_state()[0].astype(np.complex128 if model == "xy" else np.float64)
+    assert Eb == pytest.approx(oracle.energies(J, g, oracle.project(psi))[rb], rel=1e-9, abs=1e-9)
+    s.close()
+
+
+def test_best_ties_go_to_lowest_restart(gda):
+    # g = 0: s and -s have equal energy bit for bit; the best state appears at
+    # restarts 7 and 3 (negated) and 20 (identical): the answer is restart 3
+    n, R = 300, 64
+    J, _ = synth.sk_gaussian(n, 2)
+    J = J / math.sqrt(n)
+    s = gda.Solver(J, None, gda.ISING)
+    s.run(gda.default_params(dt=0.05, eps=0.1, prec=gda.BF16, seed=1), R, 400)
+    psi, gam, beta, step = s.get_state()
+    E = s.energy()
+    r0 = int(np.argmin(E))
+    psi2 = psi.copy()
+    psi2[7] = psi[r0]
+    psi2[3] = -psi[r0]
+    psi2[20] = psi[r0]
+    s.set_state(psi2, gam, beta, step)
+    E2 = s.energy()
+    Eb, rb, _ = s.best()
+    assert rb == int(np.argmin(E2)) == min(3, r0) and Eb == E2[rb]
+    s.close()
+
+
+def test_best_with_all_restarts_equal(gda):
+    # every restart in the same state: the ranking keeps them all and the
+    # full FP64 path answers (restart 0)
+    n, R = 200, 40
+    J, g = synth.xy_gaussian(n, 3)
+    s = gda.Solver(J, g, gda.XY)
+    s.run(gda.default_params(dt=0.05, eps=0.1, seed=1), 1, 200)
+    one = s.get_state()
+    s.set_state(np.repeat(one[0], R, axis=0), np.repeat(one[1], R, axis=0), np.repeat(one[2], R), one[3])
+    Eb, rb, _ = s.best()
+    assert rb == 0 and Eb == s.energy()[0]
+    s.close()
