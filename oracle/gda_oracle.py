@@ -65,7 +65,7 @@ __all__ = [
     "philox_generic", "philox_uniform", "box_muller", "noise_xi",
     "init_amplitudes", "rhs", "euler_step", "rk4_step", "add_noise",
     "run", "round_bf16", "best_of", "field_drive", "round_e4m3", "fp8_coupling_scales",
-    "gdmod_rhs", "gdmod_euler_step", "gdmod_run",
+    "gdmod_rhs", "gdmod_euler_step", "gdmod_run", "potts_roots",
 ]
 
 # --------------------------------------------------------------------------
@@ -89,6 +89,8 @@ class Params:
     noise_D: float = 0.0          # noise strength D, Eq. (2)
     noise_decay: int = 0          # 1: D_r = D max(0, 1 - mean rho / rho_th)
     h2: float = 0.0               # q=2 resonant drive (model 'ising_h2' only)
+    q: int = 0                    # resonant drive order q >= 2 of h_q conj(psi)^(q-1) (0: none)
+    hq: float = 0.0               # its strength h_q (complex models; 'potts' projects onto q-th roots)
     seed: int = 0
     init_mode: int = 1            # 0: psi = 0, 1: seeded U(-a, a) per component
     init_amp: float = 1e-3
@@ -147,10 +149,31 @@ def hamiltonian_int(J: np.ndarray, s: np.ndarray) -> int:
     return -sum(int(si[i]) * row[i] for i in range(len(row)))
 
 
-def project(psi: np.ndarray) -> np.ndarray:
+def potts_roots(q: int) -> np.ndarray:
+    """The q spin values of the q-state Potts model of Sec. 1: exp(2 pi i k / q),
+    evaluated as a quarter-turn rotation of cos / sin of the remaining angle
+    (|angle| <= pi / 4), so that quarter turns are exact (1, i, -1, -i)."""
+    x = np.mod(2.0 * np.arange(q) / q, 2.0)     # angle / pi
+    n = np.round(2.0 * x)                        # nearest quarter turn
+    f = np.pi * (x - n / 2.0)
+    c, s = np.cos(f), np.sin(f)
+    n = n.astype(int) % 4
+    re = np.select([n == 0, n == 1, n == 2, n == 3], [c, -s, -c, s])
+    im = np.select([n == 0, n == 1, n == 2, n == 3], [s, c, -s, -c])
+    return re + 1j * im
+
+
+def project(psi: np.ndarray, q: int = 0) -> np.ndarray:
     """Spin projection of amplitudes: sign(psi) for real psi (sign(0) = +1);
-    psi / |psi| for complex psi (1 where psi = 0)."""
+    psi / |psi| for complex psi (1 where psi = 0).  With q >= 2 (Potts, Sec. 1)
+    the nearest q-th root of unity: the k maximising Re(conj(w_k) psi), ties
+    to the lowest k (psi = 0 gives k = 0)."""
     psi = np.asarray(psi)
+    if q >= 2:
+        w = potts_roots(q)
+        z = np.asarray(psi, dtype=np.complex128)
+        score = np.real(z)[..., None] * np.real(w) + np.imag(z)[..., None] * np.imag(w)
+        return w[np.argmax(score, axis=-1)]
     if np.iscomplexobj(psi):
         mag = np.abs(psi)
         out = np.ones_like(psi)
@@ -368,7 +391,8 @@ def rhs(psi, gamma, beta, J0, h1, p: Params, model: str):
     """Time derivatives (f, u, v) of (psi, gamma, beta).
 
     f_i = psi_i (gamma_i - |psi_i|^2) + beta sum_{j != i} J_ij psi_j + h_1i
-          [+ h_2 conj(psi_i) in model 'ising_h2']                 (Eq. 2)
+          [+ h_2 conj(psi_i) in model 'ising_h2']
+          [+ h_q conj(psi_i)^(q-1) for complex amplitudes, p.q >= 2]  (Eq. 2)
     u_i = eps (rho_th - |psi_i|^2)                                  (Eq. 5)
     v   = eps_hat (1 - beta)                                        (Eq. 6, Delta = 1)
     psi: (R, N); gamma: (R, N); beta: (R,).  J0 has a zero diagonal."""
@@ -382,6 +406,8 @@ def rhs(psi, gamma, beta, J0, h1, p: Params, model: str):
     f = psi * (gamma - rho) + beta[:, None] * Y + h1[None, :]
     if model == "ising_h2":
         f = f + p.h2 * np.conj(psi)
+    if p.q >= 2 and p.hq != 0.0 and np.iscomplexobj(psi):
+        f = f + p.hq * np.conj(psi) ** (p.q - 1)
     u = p.eps * (p.rho_th - rho)
     v = p.eps_hat * (1.0 - beta)
     return f, u, v
@@ -431,7 +457,9 @@ def run(J, g, model: str, p: Params, R: int, steps: int, state=None, step0: int 
     """Evolve R restarts for `steps` steps of the GD algorithm (Eqs. 2, 5, 6).
 
     model: 'ising' (real amplitudes), 'xy' (complex), 'ising_h2' (complex with
-    the h_2 Psi* penalty of Sec. 3).  `state` = (psi, gamma, beta) resumes a
+    the h_2 Psi* penalty of Sec. 3); 'xy' with p.q >= 2 and p.hq > 0 is the
+    q-state Potts model of Sec. 1 (the trace projects onto the q-th roots).
+    `state` = (psi, gamma, beta) resumes a
     run at global step `step0`; otherwise the initial state is set by
     p.init_mode (0: psi = 0, 1: seeded uniform), gamma = gamma0, beta = beta0.
     If p.energy_every = k > 0, after every k-th step the best Eq. (1) energy of
@@ -460,7 +488,7 @@ def run(J, g, model: str, p: Params, R: int, steps: int, state=None, step0: int 
         psi_new = add_noise(new[0], psi, n, p, complex_)
         psi, gamma, beta = psi_new, new[1], new[2]
         if p.energy_every and trace is not None and (n + 1 - step0) % p.energy_every == 0:
-            E = energies(J, g, project(psi))
+            E = energies(J, g, project(psi, p.q if complex_ else 0))
             trace.append((n + 1,) + best_of(E))
     return psi, gamma, beta
 

@@ -267,3 +267,64 @@ def test_fp8_coupling_within_e4m3_rounding_bound():
     # saturation: amplitudes beyond 448 / 64 = 7 are clipped
     X2 = np.full((1, n), 10.0)
     assert np.allclose(fp8_coupling(J0, X2), fp8_coupling(J0, np.full((1, n), 7.0)))
+
+
+@pytest.mark.parametrize("q", [2, 3, 4, 5])
+def test_resonant_drive_matches_density_phase_form(q):
+    # Eqs. (3)-(4) with one resonant term: the q:1 drive h_q conj(psi)^(q-1)
+    # adds h_q rho^(q/2) cos(q th) to rho'/2 and -h_q rho^(q/2-1) sin(q th) to th'
+    n = 6
+    J, g = synth.xy_gaussian(n, 5, field=0.3)
+    psi = synth.initial_amplitudes(n, 1, 9, 1.1, True)[0]
+    gam = synth.normal(2, n)
+    p = Params(rho_th=1.2, q=q, hq=0.7)
+    h1 = field_drive(g, p.rho_th)
+    f0 = rhs(psi[None], gam[None], np.ones(1), coupling_operand(J), h1, Params(rho_th=1.2), "xy")[0][0]
+    f = rhs(psi[None], gam[None], np.ones(1), coupling_operand(J), h1, p, "xy")[0][0]
+    d = f - f0
+    rho, th = np.abs(psi) ** 2, np.angle(psi)
+    assert np.allclose(np.real(np.conj(psi) * d), 0.7 * rho ** (q / 2) * np.cos(q * th), rtol=1e-12, atol=1e-13)
+    assert np.allclose(np.imag(np.conj(psi) * d) / rho, -0.7 * rho ** (q / 2 - 1) * np.sin(q * th),
+                       rtol=1e-12, atol=1e-13)
+
+
+@pytest.mark.parametrize("q", [2, 3, 5, 6])
+def test_potts_projection_nearest_root(q):
+    w = oracle.potts_roots(q)
+    assert np.allclose(np.abs(w), 1.0) and np.allclose(w ** q, 1.0)
+    rng = np.random.default_rng(q)
+    th = rng.uniform(-np.pi, np.pi, 500)
+    z = rng.uniform(0.1, 3.0, 500) * np.exp(1j * th)
+    s = oracle.project(z, q)
+    k = np.mod(np.round(th * q / (2 * np.pi)), q).astype(int)  # nearest root by angle
+    assert np.allclose(s, w[k])
+    assert oracle.project(np.array([0j]), q)[0] == w[0]
+    assert np.array_equal(oracle.project(np.array([2.0 + 0j, -3.0 + 0j]), 2), np.array([1.0, -1.0]))
+
+
+def test_resonant_drive_locks_single_spin_phase():
+    # one uncoupled spin, gain fixed: the phase settles on the nearest multiple
+    # of 2 pi / q (th' = -h_q rho^(q/2-1) sin(q th) drives sin(q th) to 0 stably
+    # at the roots)
+    q = 3
+    th0 = np.array([0.3, 1.8, -2.5, 2.2])
+    psi0 = 0.8 * np.exp(1j * th0)
+    J = np.zeros((4, 4))
+    p = Params(dt=0.01, eps=0.0, q=q, hq=0.5, gamma0=1.0, init_mode=0)
+    psi, _, _ = run(J, None, "xy", p, 1, 4000, state=(psi0[None], np.ones((1, 4)), np.ones(1)))
+    want = np.exp(2j * np.pi * np.mod(np.round(th0 * q / (2 * np.pi)), q) / q)
+    assert np.allclose(psi[0] / np.abs(psi[0]), want, atol=1e-6)
+
+
+def test_potts_gd_finds_brute_force_ground_state():
+    # q = 3 Potts (XY energy of Eq. 1 with phases 2 pi k / 3), N = 7: all 3^7
+    # configurations enumerated; GD with the q:1 drive reaches the minimum
+    q, n = 3, 7
+    J, _ = synth.xy_gaussian(n, 11)
+    w = oracle.potts_roots(q)
+    ks = np.array(np.meshgrid(*[np.arange(q)] * n, indexing="ij")).reshape(n, -1).T
+    E_all = energies(J, np.zeros(n), w[ks])
+    p = Params(dt=0.02, eps=0.1, q=q, hq=2.0, init_amp=0.1, seed=3)
+    psi, _, _ = run(J, None, "xy", p, 32, 3000)
+    E = energies(J, np.zeros(n), oracle.project(psi, q))
+    assert E.min() == pytest.approx(E_all.min(), abs=1e-9)
