@@ -105,6 +105,16 @@ typedef struct {
   int32_t coupling;     /* gda_coupling_mode: GD (K = beta J) or GD-mod        */
   int32_t reserved;     /* 0                                                   */
   double gamma_c;       /* GD-mod: loss rate, gamma^inj = gamma + gamma_c      */
+  int32_t q;            /* resonant q:1 drive of Eq. (2), h_q conj(psi)^(q-1),
+                           for GDA_XY contexts: 0 none, 2 <= q <= 16.  With
+                           q >= 2 the energies, the trace and gda_best project
+                           onto the q-th roots of unity (the q-state Potts
+                           model of Sec. 1; q = 2 is the paper's complex
+                           Ising formulation with the h_2 penalty).  Per-step
+                           GD only (not RESIDENT, not GD-mod).  The projection
+                           stays with the context until the next gda_run. */
+  int32_t reserved2;    /* 0                                                   */
+  double hq;            /* h_q of that drive                                   */
 } gda_params;
 
 /* Coupling feedback of Eq. (6).
@@ -142,7 +152,7 @@ typedef enum {
 
 /* Fills p with dt = 0.01, eps = 0.1, rho_th = 1, gamma0 = 0, beta0 = 1,
  * eps_hat = 0, noise off, Euler, FP32, init_mode 1 with a = 1e-3, seed 0,
- * GDA_COUPLING_GD, gamma_c = 1. */
+ * GDA_COUPLING_GD, gamma_c = 1, no resonant drive (q = 0, hq = 0). */
 void gda_default_params(gda_params* p);
 
 /* Creates a context for an N-spin instance on the current CUDA device.

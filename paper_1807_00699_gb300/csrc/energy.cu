@@ -13,6 +13,7 @@
 
 namespace gda {
 
+
 // ---------------------------------------------------------------- init
 __global__ void k_init_state(float* psi, float* gam, float* beta, int N, int Np, int R, int cplx, int mode,
                              float amp, float gamma0, float beta0, unsigned long long seed, const float* base) {
@@ -100,7 +101,12 @@ __global__ void k_project_op(const float* psi, T* S, int N, int Np, int R, int c
   const size_t total = size_t(R) * N;
   for (size_t idx = blockIdx.x * size_t(blockDim.x) + threadIdx.x; idx < total; idx += size_t(gridDim.x) * blockDim.x) {
     const int r = int(idx / N), i = int(idx % N);
-    if (cplx) {
+    if (cplx >= 2) {
+      double sr, si;
+      potts_project(psi[size_t(2 * r) * Np + i], psi[size_t(2 * r + 1) * Np + i], cplx, sr, si);
+      S[size_t(2 * r) * Np + i] = conv<T>(float(sr));
+      S[size_t(2 * r + 1) * Np + i] = conv<T>(float(si));
+    } else if (cplx) {
       const float re = psi[size_t(2 * r) * Np + i], im = psi[size_t(2 * r + 1) * Np + i];
       const float m = sqrtf(re * re + im * im);
       S[size_t(2 * r) * Np + i] = conv<T>(m > 0.0f ? re / m : 1.0f);
@@ -116,7 +122,10 @@ __global__ void k_project64(const float* psi, double* S, int N, int Np, int R, i
   const size_t total = size_t(R) * N;
   for (size_t idx = blockIdx.x * size_t(blockDim.x) + threadIdx.x; idx < total; idx += size_t(gridDim.x) * blockDim.x) {
     const int r = int(idx / N), i = int(idx % N);
-    if (cplx) {
+    if (cplx >= 2) {
+      potts_project(psi[size_t(2 * r) * Np + i], psi[size_t(2 * r + 1) * Np + i], cplx, S[size_t(2 * r) * Np + i],
+                    S[size_t(2 * r + 1) * Np + i]);
+    } else if (cplx) {
       const double re = psi[size_t(2 * r) * Np + i], im = psi[size_t(2 * r + 1) * Np + i];
       const double m = sqrt(re * re + im * im);
       S[size_t(2 * r) * Np + i] = m > 0.0 ? re / m : 1.0;
@@ -281,7 +290,11 @@ __global__ void k_argmin(const double* E, int R, double* bestE, int* bestR) {
 __global__ void k_best_cfg(const float* psi, const int* bestR, int N, int Np, int cplx, signed char* s8, double* th) {
   const int r = *bestR;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
-    if (cplx) {
+    if (cplx >= 2) {
+      double sr, si;
+      potts_project(psi[size_t(2 * r) * Np + i], psi[size_t(2 * r + 1) * Np + i], cplx, sr, si);
+      th[i] = atan2(si, sr);
+    } else if (cplx) {
       const double re = psi[size_t(2 * r) * Np + i], im = psi[size_t(2 * r + 1) * Np + i];
       th[i] = (re == 0.0 && im == 0.0) ? 0.0 : atan2(im, re);
     } else {
@@ -495,7 +508,12 @@ __global__ void k_project_rank(const float* psi, float* S, int N, int Np, int R,
   const size_t total = size_t(R) * N;
   for (size_t idx = blockIdx.x * size_t(blockDim.x) + threadIdx.x; idx < total; idx += size_t(gridDim.x) * blockDim.x) {
     const int r = int(idx / N), i = int(idx % N);
-    if (cplx) {
+    if (cplx >= 2) {
+      double sr, si;
+      potts_project(psi[size_t(2 * r) * Np + i], psi[size_t(2 * r + 1) * Np + i], cplx, sr, si);
+      S[size_t(2 * r) * Np + i] = float(sr);
+      S[size_t(2 * r + 1) * Np + i] = float(si);
+    } else if (cplx) {
       const double re = psi[size_t(2 * r) * Np + i], im = psi[size_t(2 * r + 1) * Np + i];
       const double m = sqrt(re * re + im * im);
       S[size_t(2 * r) * Np + i] = float(m > 0.0 ? re / m : 1.0);

@@ -78,6 +78,19 @@ __device__ __forceinline__ void gd_rhs(float xr, float xi, float gs, float yr, f
   kg = __fmul_rn(eps, __fsub_rn(rho_th, rho));
 }
 
+// Resonant q:1 drive of Eq. (2) for complex amplitudes: (kr, ki) += h_q conj(x)^(q-1).
+__device__ __forceinline__ void resonant_drive(float xr, float xi, int q, float hq, float& kr, float& ki) {
+  float pr = 1.0f, pi = 0.0f;
+  for (int k = 1; k < q; ++k) {  // p <- p conj(x)
+    const float nr = __fmaf_rn(pr, xr, __fmul_rn(pi, xi));
+    const float ni = __fmaf_rn(pi, xr, -__fmul_rn(pr, xi));
+    pr = nr;
+    pi = ni;
+  }
+  kr = __fmaf_rn(hq, pr, kr);
+  ki = __fmaf_rn(hq, pi, ki);
+}
+
 // y + a x with one rounding.
 __device__ __forceinline__ float axpy(float a, float x, float y) { return __fmaf_rn(a, x, y); }
 
@@ -123,7 +136,12 @@ __device__ __forceinline__ void epi_quad(const StepArgs& a, int i, int c0, const
       // e_i = -Re(conj(s_i) (J0 s)_i) + g_i Re(s_i), s the projection of psi^n.
       const float pr = a.psi_n[o0], pi = CPLX ? a.psi_n[o1] : 0.0f;
       float sr, si = 0.0f;
-      if (CPLX) {
+      if (CPLX && a.q >= 2) {  // Potts: the nearest q-th root, as the operand's projection
+        double dr, di;
+        potts_project(pr, pi, a.q, dr, di);
+        sr = float(dr);
+        si = float(di);
+      } else if (CPLX) {
         const float m = sqrtf(pr * pr + pi * pi);
         sr = m > 0.0f ? pr / m : 1.0f;
         si = m > 0.0f ? pi / m : 0.0f;
@@ -138,6 +156,7 @@ __device__ __forceinline__ void epi_quad(const StepArgs& a, int i, int c0, const
     const float gs = (mode == M_EULER || mode == M_RK1) ? a.gam[og] : a.gstg[og];
     float kr, ki, kg;
     gd_rhs(xr, xi, gs, yr, yi, beta_s[u], h, a.eps, a.rho_th, kr, ki, kg);
+    if (CPLX && a.q) resonant_drive(xr, xi, a.q, a.hq, kr, ki);
     float nr, ni, ng;
     if (mode == M_EULER) {
       nr = axpy(a.dt, kr, xr);

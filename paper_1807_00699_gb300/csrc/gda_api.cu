@@ -69,6 +69,7 @@ struct gda_ctx {
   int ell_maxdeg = -1;        // largest row count of the current J (-1: not built)
   bool run_sparse = false;    // steps of the current call use the sparse product
   bool run_pair = false;      // tensor-core launches of the current call use two-SM tiles
+  int potts_q = 0;            // q >= 2: spins project onto the q-th roots (last run's resonant drive)
   float* K = nullptr;  // GD-mod per-restart couplings [K_R][N][Np]
   size_t K_cap = 0;
   int K_R = 0;         // restarts K was initialised for (0: none)
@@ -106,6 +107,10 @@ struct gda_ctx {
 };
 
 namespace {
+
+// Spin projection of the energy kernels: 0 real, 1 XY (psi / |psi|), q >= 2
+// the q-th roots of unity (the last run's resonant drive).
+int pmode(const gda_ctx* c) { return c->cplx ? (c->potts_q >= 2 ? c->potts_q : 1) : 0; }
 
 gda_status fail(gda_ctx* c, gda_status s, const char* fmt, ...) {
   char buf[512];
@@ -331,6 +336,10 @@ gda_status check_params(gda_ctx* c, const gda_params* p) {
   if (p->schedule == GDA_SCHEDULE_PAIR &&
       (!(p->prec == GDA_BF16 || p->prec == GDA_FP8) || (c->Np / 128) % 2 != 0 || p->coupling != GDA_COUPLING_GD))
     return fail(c, GDA_ERR_UNSUPPORTED, "two-SM tiles need BF16 or FP8 and an even number of 128-row blocks");
+  if (p->q != 0 && (p->q < 2 || p->q > 16)) return fail(c, GDA_ERR_INVALID, "q must be 0 or 2..16");
+  if (!finite(p->hq)) return fail(c, GDA_ERR_INVALID, "non-finite hq");
+  if (p->q != 0 && (!c->cplx || p->schedule == GDA_SCHEDULE_RESIDENT || p->coupling == GDA_COUPLING_GDMOD))
+    return fail(c, GDA_ERR_UNSUPPORTED, "the resonant drive needs complex amplitudes (GDA_XY) and per-step GD");
   if (p->coupling != GDA_COUPLING_GD && p->coupling != GDA_COUPLING_GDMOD)
     return fail(c, GDA_ERR_INVALID, "unknown coupling mode %d", p->coupling);
   if (p->coupling == GDA_COUPLING_GDMOD) {
@@ -351,6 +360,8 @@ StepArgs base_args(gda_ctx* c, const gda_params* p, bool tc) {
   a.mt_count = tc ? tc_mtiles(c->N) : simt_mtiles(c->N);
   a.dt = float(p->dt); a.eps = float(p->eps); a.rho_th = float(p->rho_th); a.eps_hat = float(p->eps_hat);
   a.noise_D = float(p->noise_D);
+  a.q = c->cplx ? p->q : 0;
+  a.hq = float(p->hq);
   a.noise_decay = p->noise_decay ? 1 : 0;
   a.seed = p->seed;
   a.acc = c->acc; a.gam = c->gam; a.gstg = c->gstg; a.gacc = c->gacc;
@@ -383,10 +394,10 @@ gda_status track(gda_ctx* c, const gda_params* p, bool tc, long long step) {
   a.psi_n = c->psi[c->cur];
   a.beta_in = c->beta[c->bcur];
   if (tc) {
-    LK(launch_project_bf16(c->psi[c->cur], c->ops + size_t(2) * c->Cp * c->Np, c->N, c->Np, c->R, c->cplx,
+    LK(launch_project_bf16(c->psi[c->cur], c->ops + size_t(2) * c->Cp * c->Np, c->N, c->Np, c->R, pmode(c),
                            c->stream));
   } else {
-    LK(launch_project_f32(c->psi[c->cur], c->S32, c->N, c->Np, c->R, c->cplx, c->stream));
+    LK(launch_project_f32(c->psi[c->cur], c->S32, c->N, c->Np, c->R, pmode(c), c->stream));
   }
   gda_status s = launch_step(c, a, tc, c->S32, 2);
   if (s != GDA_OK) return s;
@@ -440,7 +451,7 @@ gda_status compute_energies(gda_ctx* c) {
                          c->stream));
   } else {
     LK(launch_energy64(c->psi[c->cur], c->J64, c->g64, c->S64, c->part64, c->E64, c->N, c->Np, c->R, c->Rp, c->C,
-                       c->cplx, c->stream));
+                       pmode(c), c->stream));
   }
   return GDA_OK;
 }
@@ -481,6 +492,8 @@ void gda_default_params(gda_params* p) {
   p->init_amp = 1e-3;
   p->coupling = GDA_COUPLING_GD;
   p->gamma_c = 1.0;
+  p->q = 0;
+  p->hq = 0.0;
 }
 
 const char* gda_status_string(gda_status s) {
@@ -619,6 +632,7 @@ gda_status gda_run(gda_ctx* c, const gda_params* p, int32_t R, int64_t steps) {
   const bool f8 = p->prec == GDA_FP8;
   c->run_sparse = false;
   c->run_pair = p->schedule == GDA_SCHEDULE_PAIR;
+  c->potts_q = (c->cplx && p->q >= 2) ? p->q : 0;
   if (p->prec == GDA_SPARSE && p->coupling != GDA_COUPLING_GDMOD) {
     s = ensure_ell(c);
     if (s != GDA_OK) return s;
@@ -662,7 +676,7 @@ gda_status gda_run(gda_ctx* c, const gda_params* p, int32_t R, int64_t steps) {
   const size_t opsz = cn;
   // Resident persistent kernel: BF16 Euler runs whose tiles all fit on the
   // device at once run as one launch per tracking segment.
-  const bool resident = p->prec == GDA_BF16 && p->integ == GDA_EULER && (p->schedule == GDA_SCHEDULE_AUTO || p->schedule == GDA_SCHEDULE_RESIDENT) &&
+  const bool resident = p->prec == GDA_BF16 && p->integ == GDA_EULER && p->q == 0 && (p->schedule == GDA_SCHEDULE_AUTO || p->schedule == GDA_SCHEDULE_RESIDENT) &&
                         res_fits(c->N, c->C, c->dev) &&
                         (long long)((c->C + 127) / 128) * ((c->N + 127) / 128) <= kMaxResidentTiles;
   if (p->schedule == GDA_SCHEDULE_RESIDENT && !resident)
@@ -804,14 +818,14 @@ gda_status best_ranked(gda_ctx* c, bool* done) {
   const double delta64 = 1e-9 * (c->abs_sum + std::fabs(c->diag)) + 1e-300;
   const double margin = 2.0 * (delta + delta64);
   LK(launch_rank(c->psi[c->cur], c->J32, c->g64, c->S32, c->part64, c->E32, c->cidx, c->d_count, c->N, c->Np, c->R,
-                 c->Rp, c->C, c->cplx, c->diag, margin, c->stream));
+                 c->Rp, c->C, pmode(c), c->diag, margin, c->stream));
   int count = 0;
   CK(cudaMemcpyAsync(&count, c->d_count, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   if (count < 1 || count > c->R / 2) return GDA_OK;
   LK(launch_gather_cols(c->psi[c->cur], c->Np, c->cidx, count, c->cplx, c->stg[0], c->stream));
   LK(launch_energy64(c->stg[0], c->J64, c->g64, c->S64, c->part64, c->E64, c->N, c->Np, count, c->Rp,
-                     count * (c->cplx ? 2 : 1), c->cplx, c->stream));
+                     count * (c->cplx ? 2 : 1), pmode(c), c->stream));
   LK(launch_argmin(c->E64, count, c->bestE, c->bestR, c->stream));
   LK(launch_map_best(c->cidx, c->bestR, c->stream));
   *done = true;
@@ -834,7 +848,7 @@ gda_status gda_best(gda_ctx* c, double* E, int32_t* r, void* cfg) {
   CK(cudaMemcpyAsync(&e, c->bestE, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaMemcpyAsync(&rr, c->bestR, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   if (cfg) {
-    LK(launch_best_cfg(c->psi[c->cur], c->bestR, c->N, c->Np, c->cplx, c->cfg8, c->cfgth, c->stream));
+    LK(launch_best_cfg(c->psi[c->cur], c->bestR, c->N, c->Np, pmode(c), c->cfg8, c->cfgth, c->stream));
     if (c->cplx)
       CK(cudaMemcpyAsync(cfg, c->cfgth, size_t(c->N) * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     else

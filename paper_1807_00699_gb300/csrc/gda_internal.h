@@ -3,6 +3,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <cfloat>
 #include <cstdint>
 
 namespace gda {
@@ -58,6 +59,8 @@ struct StepArgs {
   int op_pitch;          // row pitch (elements) of op_out; Np except in packed batches
   unsigned char* op8_out;  // E4M3 copy of the next GEMM operand (FP8 path), or nullptr
   float op8_inv;         // 1 / scale of the FP8 amplitude operand
+  int q;                 // resonant drive h_q conj(psi)^(q-1) of Eq. (2) (complex only; 0: none)
+  float hq;
   const float* row_scale;  // FP8 path: Y_i = row_scale[i] * (J8 X8)_i, else nullptr
   const float* h1;       // drive h_1i = -g_i sqrt(rho_th), [Np]
   const float* beta_in;  // beta^n [Rp]
@@ -101,6 +104,26 @@ cudaError_t launch_step_tc(const TcPlan* plan, const StepArgs& a, int op_buf, cu
 cudaError_t tc_plan8_create(TcPlan** plan, const unsigned char* J8, int Np, const unsigned char* ops8, int n_op_bufs,
                             int Cp);
 cudaError_t launch_step_tc8(const TcPlan* plan, const StepArgs& a, int op_buf, cudaStream_t s, bool pair = false);
+// q-state Potts projection (Sec. 1), in double: the q-th root of unity w_k = exp(2 pi i k / q)
+// maximising Re(conj(w_k) psi); ties and psi = 0 go to the lowest k.  In the
+// projection kernels the `cplx` argument is 0 (real spins), 1 (XY: psi / |psi|)
+// or q >= 2 (Potts onto the q-th roots).
+__device__ __forceinline__ void potts_project(double re, double im, int q, double& sr, double& si) {
+  double bs = -DBL_MAX;
+  sr = 1.0;
+  si = 0.0;
+  for (int k = 0; k < q; ++k) {
+    double sn, cs;
+    sincospi(2.0 * k / q, &sn, &cs);
+    const double sc = re * cs + im * sn;
+    if (sc > bs) {
+      bs = sc;
+      sr = cs;
+      si = sn;
+    }
+  }
+}
+
 constexpr float kFp8PsiScale = 1.0f / 64.0f;
 // J8_ij = e4m3(J32_ij / s_i), s_i = max_j |J32_ij| / 448 (1 for a zero row).
 cudaError_t launch_prepare_J8(const float* J32, int Np, unsigned char* J8, float* scale, cudaStream_t s);

@@ -116,7 +116,12 @@ __device__ __forceinline__ void epi_chunk(const StepArgs& a, int i, int c0, cons
     if (MODE == M_ENERGY) {
       const float pr = R.x[k0], pi = CPLX ? R.x[k0 + 1] : 0.0f;
       float sr, si = 0.0f;
-      if (CPLX) {
+      if (CPLX && a.q >= 2) {  // Potts: the nearest q-th root, as the operand's projection
+        double dr, di;
+        potts_project(pr, pi, a.q, dr, di);
+        sr = float(dr);
+        si = float(di);
+      } else if (CPLX) {
         const float m = sqrtf(pr * pr + pi * pi);
         sr = m > 0.0f ? pr / m : 1.0f;
         si = m > 0.0f ? pi / m : 0.0f;
@@ -130,6 +135,7 @@ __device__ __forceinline__ void epi_chunk(const StepArgs& a, int i, int c0, cons
     const float gs = R.gs[u];
     float kr, ki, kg;
     gd_rhs(xr, xi, gs, yr, yi, beta_s[u], h, a.eps, a.rho_th, kr, ki, kg);
+    if (CPLX && a.q) resonant_drive(xr, xi, a.q, a.hq, kr, ki);
     float nr, ni, ng;
     if (MODE == M_EULER) {
       nr = axpy(a.dt, kr, xr);

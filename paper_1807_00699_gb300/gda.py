@@ -36,7 +36,8 @@ class Params(ct.Structure):
                 ("eps_hat", ct.c_double), ("noise_D", ct.c_double), ("noise_decay", ct.c_int32),
                 ("energy_every", ct.c_int32), ("seed", ct.c_uint64), ("init_mode", ct.c_int32),
                 ("schedule", ct.c_int32), ("init_amp", ct.c_double), ("coupling", ct.c_int32),
-                ("reserved", ct.c_int32), ("gamma_c", ct.c_double)]
+                ("reserved", ct.c_int32), ("gamma_c", ct.c_double), ("q", ct.c_int32), ("reserved2", ct.c_int32),
+                ("hq", ct.c_double)]
 
 
 SIGNATURES = {

@@ -45,7 +45,7 @@ def test_default_params(lib):
     p = gda.default_params()
     assert (p.dt, p.eps, p.rho_th, p.beta0, p.eps_hat, p.noise_D) == (0.01, 0.1, 1.0, 1.0, 0.0, 0.0)
     assert p.integ == gda.EULER and p.prec == gda.FP32 and p.init_mode == 1
-    assert ct.sizeof(gda.Params) == 112
+    assert ct.sizeof(gda.Params) == 128
 
 
 def test_status_strings(lib):

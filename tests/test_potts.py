@@ -1,0 +1,119 @@
+"""The resonant q:1 drive of Eq. (2) (h_q conj(psi)^(q-1)) and the q-state
+Potts projection of Sec. 1 through the C ABI against the FP64 oracle; q = 2 is
+the paper's complex-amplitude Ising formulation with the h_2 penalty."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gda():
+    import torch
+
+    import __graft_entry__
+    assert torch.cuda.is_available()
+    __graft_entry__.build()
+    from paper_1807_00699_gb300 import gda as mod
+    return mod
+
+
+def amp_err(psi, ref):
+    num = np.abs(psi - ref).max(axis=1)
+    den = np.maximum(np.abs(ref).max(axis=1), 1e-3)
+    return (num / den).max()
+
+
+@pytest.mark.parametrize("q,prec", [(3, "fp32"), (4, "fp32"), (2, "fp32"), (5, "sparse")])
+def test_resonant_200_steps_match_oracle(gda, q, prec):
+    n, R = 200, 24
+    if prec == "sparse":
+        J, _ = synth.sparse_3regular(n, 2)
+        J, g = J / 10.0, synth.xy_gaussian(n, 2)[1]
+    else:
+        J, g = synth.xy_gaussian(n, 6)
+    # for q >= 4 the drive grows faster than the cubic saturation: keep h_q small
+    kw = dict(dt=0.02, eps=0.2, q=q, hq=0.4 if q < 5 else 0.2, init_amp=0.3, seed=5)
+    s = gda.Solver(J, g, gda.XY)
+    s.run(gda.default_params(prec=gda.SPARSE if prec == "sparse" else gda.FP32, **kw), R, 200)
+    psi = s.get_state()[0]
+    ref = oracle.run(J, g, "xy", oracle.Params(**kw), R, 200)[0]
+    assert amp_err(psi, ref) < 1e-4
+    s.close()
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp8"])
+def test_resonant_one_tensor_core_step(gda, prec):
+    n, R = 300, 40
+    J, g = synth.xy_gaussian(n, 9)
+    psi0 = synth.initial_amplitudes(n, R, 2, 0.6, True)
+    gam0 = np.zeros((R, n))
+    s = gda.Solver(J, g, gda.XY)
+    s.set_state(psi0, gam0, np.ones(R), 0)
+    p = gda.BF16 if prec == "bf16" else gda.FP8
+    s.run(gda.default_params(dt=0.02, eps=0.2, prec=p, q=3, hq=0.8, init_mode=2), R, 1)
+    ref = oracle.run(J, g, "xy", oracle.Params(dt=0.02, eps=0.2, q=3, hq=0.8, operand=prec), R, 1,
+                     state=(psi0, gam0, np.ones(R)))[0]
+    assert amp_err(s.get_state()[0], ref) < 1e-5
+    s.close()
+
+
+@pytest.mark.parametrize("q", [3, 5])
+def test_potts_energies_trace_and_best(gda, q):
+    n, R = 257, 48
+    J, g = synth.xy_gaussian(n, 12)
+    kw = dict(dt=0.05, eps=0.1, q=q, hq=1.0 if q < 5 else 0.15, init_amp=0.2, seed=7, energy_every=50)
+    s = gda.Solver(J, g, gda.XY)
+    s.run(gda.default_params(**kw), R, 200)
+    tr = []
+    oracle.run(J, g, "xy", oracle.Params(**kw), R, 200, trace=tr)
+    steps, Et, _ = s.trace()
+    assert list(steps) == [t[0] for t in tr]
+    assert np.allclose(Et, [t[1] for t in tr], rtol=1e-4)
+    psi = s.get_state()[0].astype(np.complex128)
+    spins = oracle.project(psi, q)
+    E = s.energy()
+    assert np.allclose(E, oracle.energies(J, g, spins), rtol=1e-9, atol=1e-9)
+    Eb, rb, th = s.best()
+    assert rb == int(np.argmin(E)) and Eb == E[rb]
+    assert np.allclose(np.exp(1j * np.asarray(th)), spins[rb], atol=1e-12)  # the returned phases are roots
+    s.close()
+
+
+def test_complex_ising_h2_reaches_binary_phases(gda):
+    # the paper's Ising formulation (Sec. 3): complex amplitudes with h_2 above
+    # max_i sum_j |J_ij| lock every phase to 0 or pi; the q = 2 projection then
+    # gives the Ising spins sign(Re psi) and their Eq. (1) energies
+    n, R = 64, 32
+    J = synth.ising_pm1(n, 4)[0] / np.sqrt(n)
+    h2 = 1.1 * np.abs(J).sum(axis=1).max()
+    s = gda.Solver(J, None, gda.XY)
+    s.run(gda.default_params(dt=0.01, eps=0.1, q=2, hq=h2, init_amp=0.1, seed=3), R, 3000)
+    psi = s.get_state()[0].astype(np.complex128)
+    assert np.all(np.abs(np.sin(np.angle(psi))) < 1e-3)
+    ising = np.where(psi.real >= 0, 1.0, -1.0)
+    assert np.allclose(s.energy(), oracle.energies(J, np.zeros(n), ising), rtol=1e-12, atol=1e-9)
+    s.close()
+
+
+def test_resonant_drive_rejections(gda):
+    J, g = synth.xy_gaussian(40, 1)
+    s = gda.Solver(J, g, gda.ISING)
+    with pytest.raises(gda.GdaError) as e:
+        s.run(gda.default_params(q=2, hq=1.0), 4, 1)
+    assert e.value.status == 6
+    s.close()
+    s = gda.Solver(J, g, gda.XY)
+    for kw in (dict(schedule=gda.RESIDENT, prec=gda.BF16), dict(coupling=gda.GDMOD)):
+        with pytest.raises(gda.GdaError) as e:
+            s.run(gda.default_params(q=3, hq=1.0, **kw), 4, 1)
+        assert e.value.status == 6
+    with pytest.raises(gda.GdaError) as e:
+        s.run(gda.default_params(q=1, hq=1.0), 4, 1)
+    assert e.value.status == 1
+    # AUTO with BF16 and a resonant drive runs per step (the resident kernel has none)
+    s.run(gda.default_params(q=3, hq=1.0, prec=gda.BF16), 4, 3)
+    s.close()
