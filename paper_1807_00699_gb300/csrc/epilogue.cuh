@@ -98,14 +98,17 @@ __device__ __forceinline__ float axpy(float a, float x, float y) { return __fmaf
 // of the quad's restarts (4 Ising, 2 XY).  red[u] receives |psi^{n+1}|^2
 // (completed steps) or the restart's Eq. (1) contribution of spin i (energy
 // mode); 0 for padded restarts.  bad is set for a non-finite amplitude.
-template <bool CPLX>
+// TSTORE: also write the quad's next operand values to a.opT_out (spin-major).
+// MODE: the launch's mode (a compile-time copy of a.mode, so that each mode's
+// kernel holds only its own branch).
+template <bool CPLX, bool TSTORE, int MODE>
 __device__ __forceinline__ void epi_quad(const StepArgs& a, int i, int c0, const float y[4],
                                          const float* beta_s, const float* dsc, float red[4],
                                          int& bad) {
   constexpr int U = CPLX ? 2 : 4;
   constexpr int W = CPLX ? 2 : 1;
   const int Np = a.Np;
-  const int mode = a.mode;
+  constexpr int mode = MODE;
   const int r0 = CPLX ? (c0 >> 1) : c0;
   float z[4] = {0.f, 0.f, 0.f, 0.f};
   if (step_completes(mode)) {
@@ -115,6 +118,7 @@ __device__ __forceinline__ void epi_quad(const StepArgs& a, int i, int c0, const
     if (any) philox_normal4(uint32_t(i), uint32_t(c0 >> 2), a.step, 0u, a.seed, z);
   }
   const float h = a.h1[i];
+  float t4[4] = {0.f, 0.f, 0.f, 0.f};  // the quad's next operand values (spin-major copy)
 #pragma unroll
   for (int u = 0; u < U; ++u) {
     const int r = r0 + u;
@@ -185,6 +189,10 @@ __device__ __forceinline__ void epi_quad(const StepArgs& a, int i, int c0, const
         const float sr = axpy(cf, kr, pr), si = axpy(cf, ki, pi);
         a.xs_next[o0] = sr;
         if (CPLX) a.xs_next[o1] = si;
+        if (TSTORE) {
+          t4[u * W] = sr;
+          if (CPLX) t4[u * W + 1] = si;
+        }
         a.gstg[og] = axpy(cf, kg, gn);
         if (a.op_out) {
           a.op_out[o0] = __float2bfloat16_rn(sr);
@@ -199,6 +207,10 @@ __device__ __forceinline__ void epi_quad(const StepArgs& a, int i, int c0, const
     a.psi_out[o0] = nr;
     if (CPLX) a.psi_out[o1] = ni;
     a.gam[og] = ng;
+    if (TSTORE) {
+      t4[u * W] = nr;
+      if (CPLX) t4[u * W + 1] = ni;
+    }
     if (a.op_out) {
       a.op_out[o0] = __float2bfloat16_rn(nr);
       if (CPLX) a.op_out[o1] = __float2bfloat16_rn(ni);
@@ -207,6 +219,8 @@ __device__ __forceinline__ void epi_quad(const StepArgs& a, int i, int c0, const
     red[u] = rn;
     bad |= !(rn < 1e30f);
   }
+  if (TSTORE && a.opT_out && mode != M_RAW && mode != M_ENERGY)
+    *reinterpret_cast<float4*>(a.opT_out + size_t(i) * a.Cp + c0) = make_float4(t4[0], t4[1], t4[2], t4[3]);
 }
 
 }  // namespace gda

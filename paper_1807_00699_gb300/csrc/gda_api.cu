@@ -68,6 +68,8 @@ struct gda_ctx {
   int* d_maxdeg = nullptr;
   int ell_maxdeg = -1;        // largest row count of the current J (-1: not built)
   bool run_sparse = false;    // steps of the current call use the sparse product
+  float* opT[3] = {nullptr, nullptr, nullptr};  // sparse: spin-major operand copies [Np][Cp]
+  size_t opT_cap = 0;
   bool run_pair = false;      // tensor-core launches of the current call use two-SM tiles
   int potts_q = 0;            // q >= 2: spins project onto the q-th roots (last run's resonant drive)
   float* K = nullptr;  // GD-mod per-restart couplings [K_R][N][Np]
@@ -376,7 +378,7 @@ StepArgs base_args(gda_ctx* c, const gda_params* p, bool tc) {
 
 gda_status launch_step(gda_ctx* c, const StepArgs& a, bool tc, const float* operand32, int op_buf) {
   if (c->run_sparse && !tc) {
-    LK(launch_step_sparse(a, c->ell_col, c->ell_val, c->ell_deg, operand32, c->stream));
+    LK(launch_step_sparse(a, c->ell_col, c->ell_val, c->ell_deg, operand32, c->ell_maxdeg, c->stream));
   } else if (a.row_scale) {
     LK(launch_step_tc8(c->plan8, a, op_buf, c->stream, c->run_pair));
   } else if (tc) {
@@ -525,6 +527,7 @@ void gda_destroy(gda_ctx* c) {
   dfree(c->stamps);
   dfree(c->K);
   dfree(c->ell_col); dfree(c->ell_val); dfree(c->ell_deg); dfree(c->d_maxdeg);
+  for (float*& t : c->opT) dfree(t);
   dfree(c->fw[0]);
   dfree(c->fw[1]);
   dfree(c->base);
@@ -668,6 +671,19 @@ gda_status gda_run(gda_ctx* c, const gda_params* p, int32_t R, int64_t steps) {
   c->rcur = 0;
   if (decay) LK(launch_rho_partials(tc, c->psi[c->cur], c->N, c->Np, c->R, c->Rp, c->cplx, c->rho[0], c->stream));
 
+  // sparse product: the gathers read a spin-major copy of the operand (the 4
+  // columns of a thread's quad in one 16-byte load), kept in step by the epilogue
+  int tcur = 0;
+  if (c->run_sparse) {
+    const size_t tn = size_t(c->Np) * c->Cp;
+    if (c->opT_cap < tn) {
+      for (float*& t : c->opT) dfree(t);
+      c->opT_cap = 0;
+      for (float*& t : c->opT) CK(dalloc(&t, tn));
+      c->opT_cap = tn;
+    }
+    LK(launch_transpose_state(c->psi[c->cur], c->Np, c->Cp, c->opT[0], c->stream));
+  }
   StepArgs base = base_args(c, p, tc);
   if (f8) {
     base.row_scale = c->jscale;
@@ -732,10 +748,15 @@ gda_status gda_run(gda_ctx* c, const gda_params* p, int32_t R, int64_t steps) {
       a.psi_out = c->psi[c->cur ^ 1];
       a.op_out = (tc && !f8) ? c->ops + (c->opcur ^ 1) * opsz : nullptr;
       a.op8_out = f8 ? c->ops8 + (c->opcur ^ 1) * opsz : nullptr;
+      if (c->run_sparse) {
+        a.opT_in = c->opT[tcur];
+        a.opT_out = c->opT[(tcur + 1) % 3];
+      }
       s = launch_step(c, a, tc, c->psi[c->cur], c->opcur);
       if (s != GDA_OK) return s;
       c->cur ^= 1;
       c->opcur ^= 1;
+      tcur = (tcur + 1) % 3;
     } else {
       const float* xin[4] = {c->psi[c->cur], c->stg[0], c->stg[1], c->stg[0]};
       float* xout[3] = {c->stg[0], c->stg[1], c->stg[0]};
@@ -748,6 +769,12 @@ gda_status gda_run(gda_ctx* c, const gda_params* p, int32_t R, int64_t steps) {
         const int in_buf = c->opcur ^ (st & 1);
         a.op_out = (tc && !f8) ? c->ops + (in_buf ^ 1) * opsz : nullptr;
         a.op8_out = f8 ? c->ops8 + (in_buf ^ 1) * opsz : nullptr;
+        if (c->run_sparse) {  // psi in T[tcur]; stages through T[A], T[B], T[A]; psi^{n+1} back to T[tcur]
+          const int A = (tcur + 1) % 3, B = (tcur + 2) % 3;
+          const int tin[4] = {tcur, A, B, A}, tout[4] = {A, B, A, tcur};
+          a.opT_in = c->opT[tin[st]];
+          a.opT_out = c->opT[tout[st]];
+        }
         s = launch_step(c, a, tc, xin[st], in_buf);
         if (s != GDA_OK) return s;
       }

@@ -59,6 +59,8 @@ struct StepArgs {
   int op_pitch;          // row pitch (elements) of op_out; Np except in packed batches
   unsigned char* op8_out;  // E4M3 copy of the next GEMM operand (FP8 path), or nullptr
   float op8_inv;         // 1 / scale of the FP8 amplitude operand
+  float* opT_out;        // sparse path: next operand, spin-major [Np][Cp] (FP32), or nullptr
+  const float* opT_in;   // sparse path: this launch's operand in that layout, or nullptr
   int q;                 // resonant drive h_q conj(psi)^(q-1) of Eq. (2) (complex only; 0: none)
   float hq;
   const float* row_scale;  // FP8 path: Y_i = row_scale[i] * (J8 X8)_i, else nullptr
@@ -88,9 +90,11 @@ int simt_mtiles(int N);
 // Sparse J0 (ELL [dmax][Np], ascending columns): the SIMT step with the SGEMM
 // replaced by a gather over the nonzeros; same tiles and epilogue.
 cudaError_t launch_step_sparse(const StepArgs& a, const int* col, const float* val, const int* deg,
-                               const float* operand, cudaStream_t s);
+                               const float* operand, int maxdeg, cudaStream_t s);
 cudaError_t launch_prepare_ell(const float* J32, int N, int Np, int dmax, int* col, float* val, int* deg, int* maxdeg,
                                cudaStream_t s);
+// out[i][c] = x[c][i] for c < Cp, i < Np (column-major state -> spin-major operand).
+cudaError_t launch_transpose_state(const float* x, int Np, int Cp, float* out, cudaStream_t s);
 
 struct TcPlan;  // opaque plan holding the tensor maps of one context
 cudaError_t tc_plan_create(TcPlan** plan, const __nv_bfloat16* J16, int Np,

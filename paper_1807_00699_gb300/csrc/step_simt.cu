@@ -22,7 +22,10 @@ struct Ell {
   const int* deg;   // [Np], 0 beyond N
 };
 
-template <bool CPLX, bool SPARSE>
+// DW (sparse): the ELL width the loop runs over, a power of two >= the largest
+// row count; entries beyond a row's count are (column 0, value 0) and add
+// exact zeros, so the sums equal those over the row's nonzeros alone.
+template <bool CPLX, bool SPARSE, int DW, int MODE>
 __global__ void __launch_bounds__(256) step_simt_kernel(StepArgs a, const float* __restrict__ J,
                                                         const float* __restrict__ X, Ell ell) {
   __shared__ __align__(16) float As[SPARSE ? 1 : BK][BM + PAD];
@@ -47,17 +50,39 @@ __global__ void __launch_bounds__(256) step_simt_kernel(StepArgs a, const float*
 
   float acc[4][4] = {};
   if (SPARSE) {
-    const int cq = n0 + 4 * ty;  // the thread's 4 columns (always < Cp)
+    constexpr int KC = DW < 1 ? 1 : (DW < 8 ? DW : 8);  // entries whose loads are issued together
+    const int cq = n0 + 4 * ty;          // the thread's 4 columns (always < Cp)
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int i = m0 + tx + 16 * q;
-      const int d = i < a.N ? ell.deg[i] : 0;
-      for (int k = 0; k < d; ++k) {
-        const size_t o = size_t(k) * Np + i;
-        const int j = ell.col[o];
-        const float v = ell.val[o];
+      if (i >= a.N) continue;
+#pragma unroll 1
+      for (int k0 = 0; k0 < DW; k0 += KC) {
+        int jj[KC];
+        float vv[KC];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) acc[q][u] = __fmaf_rn(v, X[size_t(cq + u) * Np + j], acc[q][u]);
+        for (int k = 0; k < KC; ++k) {
+          const size_t o = size_t(k0 + k) * Np + i;
+          jj[k] = ell.col[o];
+          vv[k] = ell.val[o];
+        }
+        if (a.opT_in) {  // spin-major operand: the 4 columns of spin j are one 16-byte load
+          float4 x[KC];
+#pragma unroll
+          for (int k = 0; k < KC; ++k) x[k] = *reinterpret_cast<const float4*>(a.opT_in + size_t(jj[k]) * a.Cp + cq);
+#pragma unroll
+          for (int k = 0; k < KC; ++k) {
+            acc[q][0] = __fmaf_rn(vv[k], x[k].x, acc[q][0]);
+            acc[q][1] = __fmaf_rn(vv[k], x[k].y, acc[q][1]);
+            acc[q][2] = __fmaf_rn(vv[k], x[k].z, acc[q][2]);
+            acc[q][3] = __fmaf_rn(vv[k], x[k].w, acc[q][3]);
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < KC; ++k)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc[q][u] = __fmaf_rn(vv[k], X[size_t(cq + u) * Np + jj[k]], acc[q][u]);
+        }
       }
     }
   }
@@ -95,7 +120,7 @@ __global__ void __launch_bounds__(256) step_simt_kernel(StepArgs a, const float*
     const int i = m0 + tx + 16 * q;
     if (i >= a.N) continue;
     float red[4];
-    epi_quad<CPLX>(a, i, c0, acc[q], &s_beta[lr0], &s_dsc[lr0], red, bad);
+    epi_quad<CPLX, SPARSE, MODE>(a, i, c0, acc[q], &s_beta[lr0], &s_dsc[lr0], red, bad);
 #pragma unroll
     for (int u = 0; u < U; ++u) rsum[u] += red[u];
   }
@@ -126,28 +151,54 @@ __global__ void __launch_bounds__(256) step_simt_kernel(StepArgs a, const float*
 
 int simt_mtiles(int N) { return (N + BM - 1) / BM; }
 
-cudaError_t launch_step_simt(const StepArgs& a, const float* J32, const float* operand, cudaStream_t s) {
+template <bool CPLX, bool SPARSE, int DW>
+cudaError_t launch_modes(const StepArgs& a, const float* J32, const float* operand, const Ell& ell, cudaStream_t s) {
   dim3 grid((a.C + BN - 1) / BN, simt_mtiles(a.N));
-  const Ell none{nullptr, nullptr, nullptr};
-  if (a.cplx)
-    step_simt_kernel<true, false><<<grid, 256, 0, s>>>(a, J32, operand, none);
-  else
-    step_simt_kernel<false, false><<<grid, 256, 0, s>>>(a, J32, operand, none);
+  switch (a.mode) {
+    case M_EULER: step_simt_kernel<CPLX, SPARSE, DW, M_EULER><<<grid, 256, 0, s>>>(a, J32, operand, ell); break;
+    case M_RK1: step_simt_kernel<CPLX, SPARSE, DW, M_RK1><<<grid, 256, 0, s>>>(a, J32, operand, ell); break;
+    case M_RK2: step_simt_kernel<CPLX, SPARSE, DW, M_RK2><<<grid, 256, 0, s>>>(a, J32, operand, ell); break;
+    case M_RK3: step_simt_kernel<CPLX, SPARSE, DW, M_RK3><<<grid, 256, 0, s>>>(a, J32, operand, ell); break;
+    case M_RK4: step_simt_kernel<CPLX, SPARSE, DW, M_RK4><<<grid, 256, 0, s>>>(a, J32, operand, ell); break;
+    case M_ENERGY: step_simt_kernel<CPLX, SPARSE, DW, M_ENERGY><<<grid, 256, 0, s>>>(a, J32, operand, ell); break;
+    case M_RAW: step_simt_kernel<CPLX, SPARSE, DW, M_RAW><<<grid, 256, 0, s>>>(a, J32, operand, ell); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
+}
+
+cudaError_t launch_step_simt(const StepArgs& a, const float* J32, const float* operand, cudaStream_t s) {
+  const Ell none{nullptr, nullptr, nullptr};
+  return a.cplx ? launch_modes<true, false, 0>(a, J32, operand, none, s)
+                : launch_modes<false, false, 0>(a, J32, operand, none, s);
+}
+
+template <int DW>
+cudaError_t launch_sparse_w(const StepArgs& a, const Ell& ell, const float* operand, cudaStream_t s) {
+  return a.cplx ? launch_modes<true, true, DW>(a, nullptr, operand, ell, s)
+                : launch_modes<false, true, DW>(a, nullptr, operand, ell, s);
 }
 
 cudaError_t launch_step_sparse(const StepArgs& a, const int* col, const float* val, const int* deg,
-                               const float* operand, cudaStream_t s) {
-  dim3 grid((a.C + BN - 1) / BN, simt_mtiles(a.N));
+                               const float* operand, int maxdeg, cudaStream_t s) {
   const Ell ell{col, val, deg};
-  if (a.cplx)
-    step_simt_kernel<true, true><<<grid, 256, 0, s>>>(a, nullptr, operand, ell);
-  else
-    step_simt_kernel<false, true><<<grid, 256, 0, s>>>(a, nullptr, operand, ell);
-  return cudaGetLastError();
+  if (maxdeg <= 4) return launch_sparse_w<4>(a, ell, operand, s);
+  if (maxdeg <= 8) return launch_sparse_w<8>(a, ell, operand, s);
+  if (maxdeg <= 16) return launch_sparse_w<16>(a, ell, operand, s);
+  if (maxdeg <= 32) return launch_sparse_w<32>(a, ell, operand, s);
+  if (maxdeg <= 64) return launch_sparse_w<64>(a, ell, operand, s);
+  return cudaErrorInvalidValue;
 }
 
 namespace {
+
+__global__ void k_transpose_state(const float* __restrict__ x, int Np, int Cp, float* __restrict__ out) {
+  __shared__ float t[32][33];
+  const int c0 = blockIdx.x * 32, i0 = blockIdx.y * 32;
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) t[k][threadIdx.x] = x[size_t(c0 + k) * Np + i0 + threadIdx.x];
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) out[size_t(i0 + k) * Cp + c0 + threadIdx.x] = t[threadIdx.x][k];
+}
 
 // One warp per row of J0 (FP32, diagonal removed, zero padding): the nonzeros
 // of row i in ascending column order go to col / val [k][Np] for k < dmax;
@@ -179,6 +230,11 @@ __global__ void k_prepare_ell(const float* __restrict__ J32, int N, int Np, int 
 }
 
 }  // namespace
+
+cudaError_t launch_transpose_state(const float* x, int Np, int Cp, float* out, cudaStream_t s) {
+  k_transpose_state<<<dim3(Cp / 32, Np / 32), dim3(32, 8), 0, s>>>(x, Np, Cp, out);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_prepare_ell(const float* J32, int N, int Np, int dmax, int* col, float* val, int* deg, int* maxdeg,
                                cudaStream_t s) {
