@@ -6,7 +6,7 @@ rho_th, initial coupling scale beta0 of the ramp).  It runs entirely in the
 library's kernels (gda_features, gda_mlp_forward / backward, gda_proposal_loss,
 gda_adam_step); this module only moves buffers and maps the network's outputs
 to parameters.  It is trained on the best configurations and fastest settings
-that plain GD runs find; the plain algorithm stays the fallback and the judge
+that plain GD runs find; the plain algorithm stays the fallback and the arbiter
 (its FP64 energies decide).
 
 Output mapping (o = network output, mean over the instance's spins for 2..4):
