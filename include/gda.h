@@ -15,7 +15,20 @@
  *   H = - sum_i sum_j J_ij cos(theta_i - theta_j) + sum_i g_i cos(theta_i),
  *
  * on the projected spins of every restart.  Ising runs use real amplitudes
- * (theta in {0, pi}); XY runs use complex amplitudes.
+ * (theta in {0, pi}); XY runs use complex amplitudes.  Options of gda_params
+ * extend this to the paper's other forms: the GD-mod coupling feedback (Eq. 6
+ * with Delta_ij = gamma_i^inj + gamma_j^inj and a coupling matrix per
+ * restart), a resonant q:1 drive h_q conj(psi)^(q-1) of Eq. (2) with spins
+ * projected onto the q-th roots of unity (the q-state Potts model; q = 2 is
+ * the complex-amplitude Ising form with the h_2 penalty), and the coupling
+ * product in FP32, BF16 or FP8 on tensor cores, or over the nonzeros of a
+ * sparse J.
+ *
+ * Typical use: gda_create (J, g, model) -> gda_run (params, R, steps) ->
+ * gda_best (lowest FP64 energy, its restart and configuration) or
+ * gda_energy (every restart's energy) -> gda_destroy.  gda_get_state /
+ * gda_set_state checkpoint and resume; gda_batch_* runs many instances of
+ * different sizes in one launch per step.
  *
  * Conventions for every entry point:
  *   - Host pointers are plain C arrays owned by the caller; the library copies
