@@ -309,8 +309,9 @@ def run_ours(args):
             e1.record(stream)
             e1.synchronize()
             st, Et, _ = solver.trace()
+            E_all = solver.energy()  # after the timed region: FP64 energies of every restart
             return {"E": E, "steps": st, "Et": Et, "t": e0.elapsed_time(e1) / 1e3, "t_pre": e0.elapsed_time(ep) / 1e3,
-                    "extra": extra}
+                    "extra": extra, "E_all": E_all}
 
         s32 = gda.Solver(J, g, gda.XY, stream=stream)
         arms = {"fp32_plain": timed_arm(s32, gda.default_params(
@@ -341,7 +342,10 @@ def run_ours(args):
             run_t = a["t"] - a["t_pre"]
             t_hit = None if len(hit) == 0 else a["t_pre"] + float(a["steps"][hit[0]]) / TTT_STEPS * run_t
             ttt[name] = {"E_best_fp64": a["E"], "ttt_s": t_hit, "run_s": a["t"],
-                         "steps_to_target": None if len(hit) == 0 else int(a["steps"][hit[0]])}
+                         "steps_to_target": None if len(hit) == 0 else int(a["steps"][hit[0]]),
+                         # share of restarts whose final FP64 energy is within 1e-3 of E*
+                         "success_prob": float(np.mean(a["E_all"] <= target)),
+                         "gap_rel": (a["E"] - Estar) / abs(Estar)}
             if name == "bf16_learned":
                 ttt[name].update({"proposal_s": a["t_pre"], "settings": a["extra"]})
         base = ttt["fp32_plain"]
