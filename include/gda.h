@@ -230,6 +230,17 @@ gda_status gda_get_state(gda_ctx* ctx, float* psi, float* gamma, float* beta, in
 gda_status gda_set_state(gda_ctx* ctx, const float* psi, const float* gamma, const float* beta,
                          int32_t R, int64_t step);
 
+/* The running best of the energy trace (S8): whenever a tracking evaluation
+ * (energy_every > 0) finds a lower energy than any before it, the library
+ * keeps that restart's amplitudes; this call evaluates the kept configuration
+ * in FP64 (exact for integer-J Ising) and returns that energy, the restart,
+ * the step of the evaluation and optionally the configuration (cfg as in
+ * gda_best).  The running best spans runs continued with init_mode 2 and is
+ * cleared by a fresh run, gda_set_state and gda_load.  GDA_ERR_STATE if no
+ * evaluation has run.  Synchronises.  (Sec. 2-3: the best state any restart
+ * visits, verified at the end.) */
+gda_status gda_best_seen(gda_ctx* ctx, double* E, int32_t* r, int64_t* step, void* cfg);
+
 /* Copies out the energy trace of the last run (host arrays of capacity cap):
  * step index, best tracking energy and its restart.  *count receives the
  * number of entries recorded (may exceed cap).  Synchronises. */

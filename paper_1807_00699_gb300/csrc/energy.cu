@@ -148,7 +148,8 @@ __global__ void k_project_int(const float* psi, int* S, int N, int Np, int R) {
 // One block.  E_r = sum_t e_part[t][r] - sum_i J_ii; records (step, E, r) of
 // the lowest E (ties: lowest r) at trace slot *count when it fits.
 __global__ void k_track_reduce(const float* e_part, int mt, int R, int Rp, double diag, long long step,
-                               long long* t_step, double* t_E, int* t_r, int cap, int* count) {
+                               long long* t_step, double* t_E, int* t_r, int cap, int* count, double* lastE,
+                               int* lastR) {
   __shared__ double sE[32];
   __shared__ int sR[32];
   double best = DBL_MAX;
@@ -173,6 +174,8 @@ __global__ void k_track_reduce(const float* e_part, int mt, int R, int Rp, doubl
     const int c = *count;
     if (c < cap) { t_step[c] = step; t_E[c] = best; t_r[c] = br; }
     *count = c + 1;
+    *lastE = best;
+    *lastR = br;
   }
 }
 
@@ -348,8 +351,50 @@ cudaError_t launch_project_bf16(const float* psi, __nv_bfloat16* S, int N, int N
 }
 
 cudaError_t launch_track_reduce(const float* e_part, int mt, int R, int Rp, double diag, long long step,
-                                long long* t_step, double* t_E, int* t_r, int cap, int* count, cudaStream_t s) {
-  k_track_reduce<<<1, 1024, 0, s>>>(e_part, mt, R, Rp, diag, step, t_step, t_E, t_r, cap, count);
+                                long long* t_step, double* t_E, int* t_r, int cap, int* count, double* lastE,
+                                int* lastR, cudaStream_t s) {
+  k_track_reduce<<<1, 1024, 0, s>>>(e_part, mt, R, Rp, diag, step, t_step, t_E, t_r, cap, count, lastE, lastR);
+  return cudaGetLastError();
+}
+
+namespace {
+
+// Running best of the energy trace: when this evaluation's lowest tracking
+// energy (*lastE, restart *lastR) is below the best so far, the restart's
+// amplitudes (W columns of Np) are copied to snap and (E, r, step) recorded.
+__global__ void k_snapshot(const float* psi, int Np, int W, const double* lastE, const int* lastR, long long step,
+                           double* snapE, int* snapR, long long* snapStep, float* snap) {
+  __shared__ int take;
+  if (threadIdx.x == 0) {
+    take = *lastE < *snapE;
+    if (take) {
+      *snapE = *lastE;
+      *snapR = *lastR;
+      *snapStep = step;
+    }
+  }
+  __syncthreads();
+  if (!take) return;
+  const float* src = psi + size_t(*lastR) * W * Np;
+  for (int k = threadIdx.x; k < W * Np; k += blockDim.x) snap[k] = src[k];
+}
+
+__global__ void k_snapshot_reset(double* snapE, int* snapR, long long* snapStep) {
+  *snapE = DBL_MAX;
+  *snapR = -1;
+  *snapStep = -1;
+}
+
+}  // namespace
+
+cudaError_t launch_snapshot(const float* psi, int Np, int W, const double* lastE, const int* lastR, long long step,
+                            double* snapE, int* snapR, long long* snapStep, float* snap, cudaStream_t s) {
+  k_snapshot<<<1, 1024, 0, s>>>(psi, Np, W, lastE, lastR, step, snapE, snapR, snapStep, snap);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_snapshot_reset(double* snapE, int* snapR, long long* snapStep, cudaStream_t s) {
+  k_snapshot_reset<<<1, 1, 0, s>>>(snapE, snapR, snapStep);
   return cudaGetLastError();
 }
 

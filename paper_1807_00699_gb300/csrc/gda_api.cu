@@ -94,6 +94,13 @@ struct gda_ctx {
   double* t_E = nullptr;
   int* t_r = nullptr;
   int* t_count = nullptr;
+  double* lastE = nullptr;     // lowest tracking energy of the latest evaluation, its restart
+  int* lastR = nullptr;
+  double* snapE = nullptr;     // running best of the trace: tracking energy, restart, step,
+  int* snapR = nullptr;        // and the restart's amplitudes [2][Np] at that step
+  long long* snapStep = nullptr;
+  float* snap = nullptr;
+  int* d_zero = nullptr;
   int* err = nullptr;
   unsigned* flags = nullptr;  // per-tile step flags of the resident kernel
   TcPlan* plan = nullptr;
@@ -236,6 +243,7 @@ gda_status load_instance(gda_ctx* c, const double* J, const double* g, cudaMemcp
   CK(cudaMemsetAsync(c->g64, 0, Np * sizeof(double), c->stream));
   if (g) CK(cudaMemcpyAsync(c->g64, g, N * sizeof(double), kind, c->stream));
   c->K_R = 0;  // a GD-mod coupling state belongs to the previous J
+  LK(launch_snapshot_reset(c->snapE, c->snapR, c->snapStep, c->stream));
   c->ell_maxdeg = -1;
   c->abs_sum = -1.0;
   CK(cudaMemsetAsync(c->d_flags, 0, sizeof(int), c->stream));
@@ -404,7 +412,9 @@ gda_status track(gda_ctx* c, const gda_params* p, bool tc, long long step) {
   gda_status s = launch_step(c, a, tc, c->S32, 2);
   if (s != GDA_OK) return s;
   LK(launch_track_reduce(c->epart, a.mt_count, c->R, c->Rp, c->diag, step, c->t_step, c->t_E, c->t_r, kTraceCap,
-                         c->t_count, c->stream));
+                         c->t_count, c->lastE, c->lastR, c->stream));
+  LK(launch_snapshot(c->psi[c->cur], c->Np, c->cplx ? 2 : 1, c->lastE, c->lastR, step, c->snapE, c->snapR,
+                     c->snapStep, c->snap, c->stream));
   return GDA_OK;
 }
 
@@ -524,6 +534,8 @@ void gda_destroy(gda_ctx* c) {
   dfree(c->bestE); dfree(c->bestR); dfree(c->cfg8); dfree(c->cfgth);
   dfree(c->E32); dfree(c->cidx); dfree(c->d_count); dfree(c->d_abs);
   dfree(c->t_step); dfree(c->t_E); dfree(c->t_r); dfree(c->t_count); dfree(c->err); dfree(c->flags);
+  dfree(c->lastE); dfree(c->lastR); dfree(c->snapE); dfree(c->snapR); dfree(c->snapStep); dfree(c->snap);
+  dfree(c->d_zero);
   dfree(c->stamps);
   dfree(c->K);
   dfree(c->ell_col); dfree(c->ell_val); dfree(c->ell_deg); dfree(c->d_maxdeg);
@@ -583,10 +595,19 @@ static gda_status create_impl(const double* J, const double* g, int32_t N, int32
   step(dalloc(&c->t_E, kTraceCap));
   step(dalloc(&c->t_r, kTraceCap));
   step(dalloc(&c->t_count, 1));
+  step(dalloc(&c->lastE, 1));
+  step(dalloc(&c->lastR, 1));
+  step(dalloc(&c->snapE, 1));
+  step(dalloc(&c->snapR, 1));
+  step(dalloc(&c->snapStep, 1));
+  step(dalloc(&c->snap, 2 * Np));
+  step(dalloc(&c->d_zero, 1));
   step(dalloc(&c->err, 1));
   step(dalloc(&c->flags, kMaxResidentTiles));
   if (st == GDA_OK) step(cudaMemset(c->err, 0, sizeof(int)));
   if (st == GDA_OK) step(cudaMemset(c->t_count, 0, sizeof(int)));
+  if (st == GDA_OK) step(cudaMemset(c->d_zero, 0, sizeof(int)));
+  if (st == GDA_OK) step(cudaMemset(c->snap, 0, 2 * Np * sizeof(float)));
   if (st == GDA_OK) step(cudaMemset(c->h1, 0, Np * sizeof(float)));
   if (st == GDA_OK) step(cudaMemset(c->g32, 0, Np * sizeof(float)));
   if (st == GDA_OK) st = load_instance(c, J, g, kind);
@@ -652,6 +673,7 @@ gda_status gda_run(gda_ctx* c, const gda_params* p, int32_t R, int64_t steps) {
     c->bcur = 0;
     c->step = 0;
     c->have_state = true;
+    LK(launch_snapshot_reset(c->snapE, c->snapR, c->snapStep, c->stream));
   }
   CK(cudaMemsetAsync(c->t_count, 0, sizeof(int), c->stream));
   LK(launch_fill_h1(c->g64, c->h1, c->N, float(std::sqrt(p->rho_th)), c->stream));
@@ -888,6 +910,38 @@ gda_status gda_best(gda_ctx* c, double* E, int32_t* r, void* cfg) {
   return GDA_OK;
 }
 
+gda_status gda_best_seen(gda_ctx* c, double* E, int32_t* r, int64_t* step, void* cfg) {
+  if (!c) return GDA_ERR_INVALID;
+  int rr = -1;
+  long long st = -1;
+  CK(cudaMemcpyAsync(&rr, c->snapR, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(&st, c->snapStep, sizeof(long long), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (rr < 0 || !c->have_state) return fail(c, GDA_ERR_STATE, "no tracked state: run with energy_every > 0 first");
+  const int W = c->cplx ? 2 : 1;
+  if (c->int_exact) {
+    LK(launch_energy_int(c->snap, c->Jint, c->Sint, c->partint, c->E64, c->N, c->Np, 1, c->Rp, W, c->stream));
+  } else {
+    LK(launch_energy64(c->snap, c->J64, c->g64, c->S64, c->part64, c->E64, c->N, c->Np, 1, c->Rp, W, pmode(c),
+                       c->stream));
+  }
+  double e = 0.0;
+  CK(cudaMemcpyAsync(&e, c->E64, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  if (cfg) {
+    LK(launch_best_cfg(c->snap, c->d_zero, c->N, c->Np, pmode(c), c->cfg8, c->cfgth, c->stream));
+    if (c->cplx)
+      CK(cudaMemcpyAsync(cfg, c->cfgth, size_t(c->N) * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    else
+      CK(cudaMemcpyAsync(cfg, c->cfg8, size_t(c->N), cudaMemcpyDeviceToHost, c->stream));
+  }
+  gda_status s = check_err(c);
+  if (s != GDA_OK) return s;
+  if (E) *E = e;
+  if (r) *r = rr;
+  if (step) *step = st;
+  return GDA_OK;
+}
+
 gda_status gda_get_state(gda_ctx* c, float* psi, float* gamma, float* beta, int64_t* step) {
   if (!c) return GDA_ERR_INVALID;
   if (!c->have_state) return fail(c, GDA_ERR_STATE, "no state");
@@ -925,6 +979,7 @@ gda_status gda_set_state(gda_ctx* c, const float* psi, const float* gamma, const
   c->cur = 0;
   c->bcur = 0;
   c->step = step;
+  LK(launch_snapshot_reset(c->snapE, c->snapR, c->snapStep, c->stream));
   c->have_state = true;
   return GDA_OK;
 }

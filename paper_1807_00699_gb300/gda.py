@@ -53,6 +53,7 @@ SIGNATURES = {
     "gda_best": (ct.c_int, [_VP, _D, ct.POINTER(ct.c_int32), _VP]),
     "gda_get_state": (ct.c_int, [_VP, _F, _F, _F, ct.POINTER(ct.c_int64)]),
     "gda_set_state": (ct.c_int, [_VP, _F, _F, _F, ct.c_int32, ct.c_int64]),
+    "gda_best_seen": (ct.c_int, [_VP, _D, ct.POINTER(ct.c_int32), ct.POINTER(ct.c_int64), _VP]),
     "gda_trace": (ct.c_int, [_VP, ct.POINTER(ct.c_int64), _D, ct.POINTER(ct.c_int32), ct.c_int32,
                              ct.POINTER(ct.c_int32)]),
     "gda_coupling": (ct.c_int, [_VP, ct.c_int32, ct.c_int32, _F, _F]),
@@ -193,6 +194,20 @@ class Solver:
             cp = cfg.ctypes.data_as(_VP)
         self._check(self._lib.gda_best(self._h, ct.byref(E), ct.byref(r), cp))
         return E.value, r.value, cfg
+
+    def best_seen(self, with_cfg: bool = True):
+        """(E, r, step, cfg) of the lowest tracked energy any restart reached
+        (gda_best_seen): the configuration kept at that step, in FP64."""
+        E = ct.c_double()
+        r = ct.c_int32()
+        st = ct.c_int64()
+        cfg = None
+        cp = None
+        if with_cfg:
+            cfg = np.empty(self.N, dtype=np.float64 if self.model == XY else np.int8)
+            cp = cfg.ctypes.data_as(_VP)
+        self._check(self._lib.gda_best_seen(self._h, ct.byref(E), ct.byref(r), ct.byref(st), cp))
+        return E.value, r.value, st.value, cfg
 
     def get_state(self):
         R, N, W = self.R, self.N, self.width
