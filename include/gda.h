@@ -212,10 +212,14 @@ gda_status gda_energy(gda_ctx* ctx, double* E);
  * synchronise. */
 gda_status gda_energy_dev(gda_ctx* ctx, double* E_dev);
 
-/* Lowest Eq. (1) energy over the restarts (ties: lowest restart index).
+/* Lowest Eq. (1) energy over the restarts (ties: lowest restart index), the
+ * same answer and FP64 value as the argmin of gda_energy.  For non-integer
+ * energies and R >= 32 it first bounds every restart's energy with
+ * compensated FP32 sums (error below 48 * 2^-24 * (sum |J0| + sum |g|)) and
+ * evaluates in FP64 only the restarts within twice that bound of the lowest.
  * E, r: host scalars (either may be NULL).  cfg (may be NULL): N int8 spins
- * (+1/-1) for Ising, or N doubles theta_i in (-pi, pi] for XY, host.
- * Synchronises. */
+ * (+1/-1) for Ising, or N doubles theta_i in (-pi, pi] for XY (on the q-th
+ * roots of unity after a run with a resonant drive), host.  Synchronises. */
 gda_status gda_best(gda_ctx* ctx, double* E, int32_t* r, void* cfg);
 
 /* Copies the state out (host).  psi: R*N floats (Ising) or R*N interleaved
