@@ -116,7 +116,12 @@ typedef struct {
   int32_t schedule;     /* gda_schedule: how BF16 steps are launched           */
   double init_amp;      /* a for init_mode 1                                   */
   int32_t coupling;     /* gda_coupling_mode: GD (K = beta J) or GD-mod        */
-  int32_t reserved;     /* 0                                                   */
+  int32_t withhold_flag; /* testing only, 0 otherwise: k >= 1 makes the last
+                           tile of the resident kernel (GDA_SCHEDULE_RESIDENT)
+                           withhold the step flag it would publish after step
+                           k of each launch, so every wait on it in its
+                           column runs out after wait_s and the run reports
+                           GDA_ERR_TIMEOUT; the context stays usable          */
   double gamma_c;       /* GD-mod: loss rate, gamma^inj = gamma + gamma_c      */
   int32_t q;            /* resonant q:1 drive of Eq. (2), h_q conj(psi)^(q-1),
                            for GDA_XY contexts: 0 none, 2 <= q <= 16.  With
@@ -128,6 +133,11 @@ typedef struct {
                            stays with the context until the next gda_run. */
   int32_t reserved2;    /* 0                                                   */
   double hq;            /* h_q of that drive                                   */
+  double wait_s;        /* limit of every device-side wait of the tensor-core
+                           step kernels, in seconds (0: about 2 s); a wait
+                           that runs out aborts the launch, which drains its
+                           copies and MMAs, frees its tensor memory and
+                           reports GDA_ERR_TIMEOUT                             */
 } gda_params;
 
 /* Coupling feedback of Eq. (6).
@@ -165,7 +175,8 @@ typedef enum {
 
 /* Fills p with dt = 0.01, eps = 0.1, rho_th = 1, gamma0 = 0, beta0 = 1,
  * eps_hat = 0, noise off, Euler, FP32, init_mode 1 with a = 1e-3, seed 0,
- * GDA_COUPLING_GD, gamma_c = 1, no resonant drive (q = 0, hq = 0). */
+ * GDA_COUPLING_GD, gamma_c = 1, no resonant drive (q = 0, hq = 0), the
+ * default wait limit (wait_s = 0) and no withheld flag. */
 void gda_default_params(gda_params* p);
 
 /* Creates a context for an N-spin instance on the current CUDA device.
@@ -245,6 +256,17 @@ gda_status gda_set_state(gda_ctx* ctx, const float* psi, const float* gamma, con
  * visits, verified at the end.) */
 gda_status gda_best_seen(gda_ctx* ctx, double* E, int32_t* r, int64_t* step, void* cfg);
 
+/* FP64 Eq. (1) energies (exact for integer-J Ising) of the configurations the
+ * trace of the last run names: trace entry k's configuration is the restart
+ * with the lowest tracking energy at that evaluation, as it was at that step
+ * (kept on the device when the evaluation ran).  E: `count` doubles (host)
+ * for entries first .. first+count-1, in trace order.  The run keeps up to
+ * min(steps / energy_every, 65536, 256 MiB / (4 N' W)) entries (N' = N
+ * rounded up to 128, W = 2 for XY, 1 for Ising); GDA_ERR_INVALID for entries
+ * beyond what was recorded and kept.  Synchronises.  (Sec. 2-3: the energy
+ * of the state a run holds at each evaluation, verified in FP64.) */
+gda_status gda_trace_energy(gda_ctx* ctx, int32_t first, int32_t count, double* E);
+
 /* Copies out the energy trace of the last run (host arrays of capacity cap):
  * step index, best tracking energy and its restart.  *count receives the
  * number of entries recorded (may exceed cap).  Synchronises. */
@@ -278,9 +300,9 @@ gda_status gda_profile_read(gda_ctx* ctx, uint64_t* out, int32_t cap_ctas, int32
  * context-based calls above allocate on gda_create / gda_run, this one never
  * calls cudaMalloc, cudaFree or any allocating routine.
  *
- * Computes the Eq. (1) energy of the projected spins of R restarts, in FP64,
- * exactly as gda_energy does, from caller-owned device buffers:
- *   J_dev   N*N doubles, row-major, symmetric (diagonal counted as in Eq. 1);
+ * Computes the same FP64 energies of the projected spins of R restarts as
+ * gda_energy does (J's diagonal counted), from caller-owned device buffers:
+ *   J_dev   N*N doubles, row-major, symmetric;
  *   g_dev   N doubles, or NULL for g = 0;
  *   psi_dev amplitudes in the gda_get_state layout: R*N floats (Ising) or
  *           R*N interleaved (re, im) float pairs (XY), restart-major;
@@ -292,7 +314,12 @@ gda_status gda_profile_read(gda_ctx* ctx, uint64_t* out, int32_t cap_ctas, int32
  * N <= GDA_NOALLOC_MAX_N and R <= GDA_NOALLOC_MAX_R return GDA_ERR_INVALID,
  * as do NULL buffers, N < 1, R < 1 or an unknown model.
  * The first call on a device looks up the array's device address (with that
- * device current); make that first call before any stream capture.  All calls
+ * device current); make that first call before any stream capture.  Under
+ * CUDA's default lazy module loading that first call is also when the module
+ * holding the array, and so the array itself, is placed in device memory: a
+ * caller that will reserve the rest of the GPU for its own pool, or freeze
+ * its allocator, makes its first call before doing so (or sets
+ * CUDA_MODULE_LOADING=EAGER, which places it when the library loads).  All calls
  * share the array: calls whose work overlaps on the GPU (different streams,
  * or different threads on one device) race and must be serialised by the
  * caller.  Asynchronous on `stream`; returns GDA_ERR_CUDA if a launch fails. */

@@ -362,8 +362,11 @@ namespace {
 // Running best of the energy trace: when this evaluation's lowest tracking
 // energy (*lastE, restart *lastR) is below the best so far, the restart's
 // amplitudes (W columns of Np) are copied to snap and (E, r, step) recorded.
+// Also keeps that restart's amplitudes in hist[entry] for the trace entry just
+// recorded (entry = *count - 1) when entry < hist_cap.
 __global__ void k_snapshot(const float* psi, int Np, int W, const double* lastE, const int* lastR, long long step,
-                           double* snapE, int* snapR, long long* snapStep, float* snap) {
+                           double* snapE, int* snapR, long long* snapStep, float* snap, float* hist, int hist_cap,
+                           const int* count) {
   __shared__ int take;
   if (threadIdx.x == 0) {
     take = *lastE < *snapE;
@@ -374,8 +377,13 @@ __global__ void k_snapshot(const float* psi, int Np, int W, const double* lastE,
     }
   }
   __syncthreads();
-  if (!take) return;
   const float* src = psi + size_t(*lastR) * W * Np;
+  const int entry = *count - 1;
+  if (hist && entry >= 0 && entry < hist_cap) {
+    float* dst = hist + size_t(entry) * W * Np;
+    for (int k = threadIdx.x; k < W * Np; k += blockDim.x) dst[k] = src[k];
+  }
+  if (!take) return;
   for (int k = threadIdx.x; k < W * Np; k += blockDim.x) snap[k] = src[k];
 }
 
@@ -388,8 +396,9 @@ __global__ void k_snapshot_reset(double* snapE, int* snapR, long long* snapStep)
 }  // namespace
 
 cudaError_t launch_snapshot(const float* psi, int Np, int W, const double* lastE, const int* lastR, long long step,
-                            double* snapE, int* snapR, long long* snapStep, float* snap, cudaStream_t s) {
-  k_snapshot<<<1, 1024, 0, s>>>(psi, Np, W, lastE, lastR, step, snapE, snapR, snapStep, snap);
+                            double* snapE, int* snapR, long long* snapStep, float* snap, float* hist, int hist_cap,
+                            const int* count, cudaStream_t s) {
+  k_snapshot<<<1, 1024, 0, s>>>(psi, Np, W, lastE, lastR, step, snapE, snapR, snapStep, snap, hist, hist_cap, count);
   return cudaGetLastError();
 }
 

@@ -19,6 +19,7 @@ using namespace gda;
 namespace {
 
 constexpr int kTraceCap = 1 << 16;
+constexpr size_t kHistBytes = size_t(256) << 20;  // bound on the kept trace configurations
 constexpr int kMaxResidentTiles = 1024;  // bound on the CTAs of a resident launch
 
 size_t round_up(size_t x, size_t m) { return (x + m - 1) / m * m; }
@@ -100,6 +101,9 @@ struct gda_ctx {
   int* snapR = nullptr;        // and the restart's amplitudes [2][Np] at that step
   long long* snapStep = nullptr;
   float* snap = nullptr;
+  float* hist = nullptr;       // tracked-best amplitudes of every trace entry [hist_cap][W][Np]
+  size_t hist_bytes = 0;
+  int hist_run = 0;            // entries the current run keeps (<= kept capacity)
   int* d_zero = nullptr;
   int* err = nullptr;
   unsigned* flags = nullptr;  // per-tile step flags of the resident kernel
@@ -347,6 +351,9 @@ gda_status check_params(gda_ctx* c, const gda_params* p) {
       (!(p->prec == GDA_BF16 || p->prec == GDA_FP8) || (c->Np / 128) % 2 != 0 || p->coupling != GDA_COUPLING_GD))
     return fail(c, GDA_ERR_UNSUPPORTED, "two-SM tiles need BF16 or FP8 and an even number of 128-row blocks");
   if (p->q != 0 && (p->q < 2 || p->q > 16)) return fail(c, GDA_ERR_INVALID, "q must be 0 or 2..16");
+  if (!finite(p->wait_s) || p->wait_s < 0 || p->wait_s > 1e3)
+    return fail(c, GDA_ERR_INVALID, "wait_s must be in [0, 1000] seconds");
+  if (p->withhold_flag < 0) return fail(c, GDA_ERR_INVALID, "withhold_flag must be >= 0");
   if (!finite(p->hq)) return fail(c, GDA_ERR_INVALID, "non-finite hq");
   if (p->q != 0 && (!c->cplx || p->schedule == GDA_SCHEDULE_RESIDENT || p->coupling == GDA_COUPLING_GDMOD))
     return fail(c, GDA_ERR_UNSUPPORTED, "the resonant drive needs complex amplitudes (GDA_XY) and per-step GD");
@@ -381,6 +388,7 @@ StepArgs base_args(gda_ctx* c, const gda_params* p, bool tc) {
   a.err = c->err;
   const long long ctas = (long long)((c->C + 127) / 128) * ((c->N + 127) / 128);
   a.stamps = (c->stamps && tc && ctas <= c->stamp_cap) ? c->stamps : nullptr;
+  a.wait_cycles = p->wait_s > 0 ? (long long)(p->wait_s * ptx_cycles_per_second()) : ptx_default_wait_cycles();
   return a;
 }
 
@@ -414,7 +422,7 @@ gda_status track(gda_ctx* c, const gda_params* p, bool tc, long long step) {
   LK(launch_track_reduce(c->epart, a.mt_count, c->R, c->Rp, c->diag, step, c->t_step, c->t_E, c->t_r, kTraceCap,
                          c->t_count, c->lastE, c->lastR, c->stream));
   LK(launch_snapshot(c->psi[c->cur], c->Np, c->cplx ? 2 : 1, c->lastE, c->lastR, step, c->snapE, c->snapR,
-                     c->snapStep, c->snap, c->stream));
+                     c->snapStep, c->snap, c->hist, c->hist_run, c->t_count, c->stream));
   return GDA_OK;
 }
 
@@ -535,6 +543,7 @@ void gda_destroy(gda_ctx* c) {
   dfree(c->E32); dfree(c->cidx); dfree(c->d_count); dfree(c->d_abs);
   dfree(c->t_step); dfree(c->t_E); dfree(c->t_r); dfree(c->t_count); dfree(c->err); dfree(c->flags);
   dfree(c->lastE); dfree(c->lastR); dfree(c->snapE); dfree(c->snapR); dfree(c->snapStep); dfree(c->snap);
+  dfree(c->hist);
   dfree(c->d_zero);
   dfree(c->stamps);
   dfree(c->K);
@@ -676,6 +685,20 @@ gda_status gda_run(gda_ctx* c, const gda_params* p, int32_t R, int64_t steps) {
     LK(launch_snapshot_reset(c->snapE, c->snapR, c->snapStep, c->stream));
   }
   CK(cudaMemsetAsync(c->t_count, 0, sizeof(int), c->stream));
+  // keep the tracked-best configuration of every trace entry of this run
+  c->hist_run = 0;
+  if (p->energy_every > 0 && steps >= p->energy_every) {
+    const size_t row = size_t(c->cplx ? 2 : 1) * c->Np * sizeof(float);
+    const size_t want = std::min<size_t>(size_t(steps / p->energy_every), size_t(kTraceCap));
+    const size_t n = std::min(want, kHistBytes / row);
+    if (c->hist_bytes < n * row) {
+      dfree(c->hist);
+      c->hist_bytes = 0;
+      CK(dalloc(reinterpret_cast<unsigned char**>(&c->hist), n * row));
+      c->hist_bytes = n * row;
+    }
+    c->hist_run = int(n);
+  }
   LK(launch_fill_h1(c->g64, c->h1, c->N, float(std::sqrt(p->rho_th)), c->stream));
   // field in FP32 for the tracking energy
   LK(launch_fill_h1(c->g64, c->g32, c->N, -1.0f, c->stream));
@@ -740,6 +763,8 @@ gda_status gda_run(gda_ctx* c, const gda_params* p, int32_t R, int64_t steps) {
       ra.rho[0] = c->rho[c->rcur];
       ra.rho[1] = c->rho[c->rcur ^ 1];
       ra.ops = c->ops;
+      ra.withhold_tile = p->withhold_flag > 0 ? int((c->C + 127) / 128) * int((c->N + 127) / 128) - 1 : -1;
+      ra.withhold_step = p->withhold_flag > 0 ? p->withhold_flag : -1;
       CK(cudaMemsetAsync(c->flags, 0, kMaxResidentTiles * sizeof(unsigned), c->stream));
       LK(launch_step_res(c->plan, ra, a, c->stream));
       c->cur ^= flip;
@@ -940,6 +965,31 @@ gda_status gda_best_seen(gda_ctx* c, double* E, int32_t* r, int64_t* step, void*
   if (r) *r = rr;
   if (step) *step = st;
   return GDA_OK;
+}
+
+gda_status gda_trace_energy(gda_ctx* c, int32_t first, int32_t count, double* E) {
+  if (!c) return GDA_ERR_INVALID;
+  if (!E || first < 0 || count < 0) return fail(c, GDA_ERR_INVALID, "E NULL, first < 0 or count < 0");
+  int n = 0;
+  CK(cudaMemcpyAsync(&n, c->t_count, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  const int kept = std::min(n, c->hist_run);
+  if (!c->have_state || int64_t(first) + count > kept)
+    return fail(c, GDA_ERR_INVALID, "trace entries [%d, %d) requested, %d kept", first, first + count, kept);
+  const int W = c->cplx ? 2 : 1;
+  // evaluate in chunks of at most R configurations (the energy scratch holds R columns)
+  for (int k0 = 0; k0 < count; k0 += c->R) {
+    const int m = std::min(c->R, count - k0);
+    const float* src = c->hist + size_t(first + k0) * W * c->Np;
+    if (c->int_exact) {
+      LK(launch_energy_int(src, c->Jint, c->Sint, c->partint, c->E64, c->N, c->Np, m, c->Rp, m * W, c->stream));
+    } else {
+      LK(launch_energy64(src, c->J64, c->g64, c->S64, c->part64, c->E64, c->N, c->Np, m, c->Rp, m * W, pmode(c),
+                         c->stream));
+    }
+    CK(cudaMemcpyAsync(E + k0, c->E64, size_t(m) * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  }
+  return check_err(c);
 }
 
 gda_status gda_get_state(gda_ctx* c, float* psi, float* gamma, float* beta, int64_t* step) {

@@ -73,6 +73,7 @@ struct StepArgs {
   float* e_part;         // [mt_count][Rp] partial energies (energy mode)
   int* err;
   unsigned long long* stamps;  // per-CTA timestamps [ctas][8], or nullptr
+  long long wait_cycles;       // limit of every device-side wait (SM clock cycles)
 };
 
 // Nanosecond device clock for the optional per-CTA timestamps.
@@ -83,6 +84,11 @@ __device__ __forceinline__ void stamp(const StepArgs& a, int k) {
     a.stamps[(size_t(blockIdx.y) * gridDim.x + blockIdx.x) * 8 + k] = t;
   }
 }
+
+// Default limit of a device-side wait (SM clock cycles, about 2 s) and the
+// cycles per second used to convert a limit given in seconds.
+long long ptx_default_wait_cycles();
+double ptx_cycles_per_second();
 
 // Launchers (return cudaGetLastError() of the launch).
 cudaError_t launch_step_simt(const StepArgs& a, const float* J32, const float* operand, cudaStream_t s);

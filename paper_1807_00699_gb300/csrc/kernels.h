@@ -21,9 +21,11 @@ cudaError_t launch_track_reduce(const float* e_part, int mt, int R, int Rp, doub
                                 long long* t_step, double* t_E, int* t_r, int cap, int* count, double* lastE,
                                 int* lastR, cudaStream_t s);
 // Running best of the trace (energy.cu): copy restart *lastR's amplitudes to
-// snap when *lastE improves on *snapE; reset before a fresh run.
+// snap when *lastE improves on *snapE; reset before a fresh run.  With hist,
+// also keep them as trace entry *count - 1 (if below hist_cap).
 cudaError_t launch_snapshot(const float* psi, int Np, int W, const double* lastE, const int* lastR, long long step,
-                            double* snapE, int* snapR, long long* snapStep, float* snap, cudaStream_t s);
+                            double* snapE, int* snapR, long long* snapStep, float* snap, float* hist, int hist_cap,
+                            const int* count, cudaStream_t s);
 cudaError_t launch_snapshot_reset(double* snapE, int* snapR, long long* snapStep, cudaStream_t s);
 cudaError_t launch_energy64(const float* psi, const double* J64, const double* g, double* S64, double* part,
                             double* E, int N, int Np, int R, int Rp, int C, int cplx, cudaStream_t s);

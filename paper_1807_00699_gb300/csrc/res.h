@@ -15,6 +15,8 @@ struct ResArgs {
   float* beta_final;        // coupling scale after the last step [Rp]
   float* rho[2];            // density partial sums: rho[0] of the first step's state
   __nv_bfloat16* ops;       // operand buffers [2][Cp][Np]
+  int withhold_tile;        // testing: tile (column block * row blocks + row block) that
+  int withhold_step;        // does not release its flag value withhold_step (-1: none)
 };
 
 // True if every CTA of the launch for N spins and C columns fits on the device at once.

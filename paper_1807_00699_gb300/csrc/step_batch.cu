@@ -236,8 +236,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         s_beta[e] = r < a.R ? a.beta_in[r] : 1.0f;
         s_dsc[e] = r < a.R ? noise_scale(a, r) : 0.0f;
       }
-      bar_epi();
-      const bool ok = __all_sync(0xffffffffu, mbar_wait(acc_full(k2), use & 1) && !*(volatile int*)&s_flag[0]);
+      // one decision for all epilogue warps (the vote is also the barrier that
+      // publishes s_beta / s_dsc)
+      const bool ok = epi_vote_all<32 * NEPI>(mbar_wait(acc_full(k2), use & 1) && !*(volatile int*)&s_flag[0]);
       tc_fence_after();
       if (!ok) {
         if (lane == 0) atomicOr(b.err, E_TIMEOUT);

@@ -12,7 +12,7 @@
 // blocks never wait on each other, and the A (coupling) tiles of the next step
 // are prefetched while the epilogue runs.  Every wait is bounded.
 //
-// Roles: warp 0 TMA producer; warp 1 TMEM allocator + MMA issuer; warps 2..9
+// Roles: warp 0 TMA producer; warp 1 TMEM allocator + MMA issuer; warps 2..17
 // epilogue (warp w reads TMEM lane quarter w % 4 and a quarter of the columns).
 // Per-element arithmetic is the Euler update of Eqs. (2), (5), (6) with the
 // same FP32 expression sequence as the per-step kernels.
@@ -41,11 +41,11 @@ constexpr uint32_t SMEM = 1024 + STAGES * STAGE_BYTES + TAIL;
 __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"n"(32 * EPI_WARPS) : "memory"); }
 
 // Bounded wait until a tile flag reaches target (acquire).
-__device__ __forceinline__ bool flag_wait(const unsigned* f, unsigned target) {
+__device__ __forceinline__ bool flag_wait(const unsigned* f, unsigned target, long long limit) {
   if (ld_acquire_gpu(f) >= target) return true;
   const long long t0 = clock64();
   while (ld_acquire_gpu(f) < target) {
-    if (clock64() - t0 > kWaitCycles) return false;
+    if (clock64() - t0 > limit) return false;
   }
   return true;
 }
@@ -76,6 +76,7 @@ __global__ void __launch_bounds__(RES_THREADS, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
   const int KB = (a.N + BK - 1) / BK;
+  const long long lim = a.wait_cycles;
   auto full_bar = [&](int s) { return smem_u32(bars + s); };
   auto empty_bar = [&](int s) { return smem_u32(bars + STAGES + s); };
   const uint32_t acc_full = smem_u32(bars + 2 * STAGES);
@@ -116,7 +117,7 @@ __global__ void __launch_bounds__(RES_THREADS, 1)
         for (int kb = 0; kb < pre; ++kb) {
           const int s = (it + kb) % STAGES;
           const uint32_t ph = ((it + kb) / STAGES) & 1;
-          if (!mbar_wait(empty_bar(s), ph ^ 1u) || *(volatile int*)&s_flag[0]) {
+          if (!mbar_wait(empty_bar(s), ph ^ 1u, lim) || *(volatile int*)&s_flag[0]) {
             stop = true;
             break;
           }
@@ -130,7 +131,7 @@ __global__ void __launch_bounds__(RES_THREADS, 1)
           const int s = it % STAGES;
           if (kb >= pre) {
             const uint32_t ph = (it / STAGES) & 1;
-            if (!mbar_wait(empty_bar(s), ph ^ 1u) || *(volatile int*)&s_flag[0]) {
+            if (!mbar_wait(empty_bar(s), ph ^ 1u, lim) || *(volatile int*)&s_flag[0]) {
               stop = true;
               break;
             }
@@ -140,7 +141,7 @@ __global__ void __launch_bounds__(RES_THREADS, 1)
           }
           const int mb = (kb * BK) / BM;  // row block that produced these spins
           if (n > 0 && mb != ready_m) {
-            if (!flag_wait(col_flags + mb, unsigned(n))) {
+            if (!flag_wait(col_flags + mb, unsigned(n), lim)) {
               stop = true;
               break;
             }
@@ -158,7 +159,7 @@ __global__ void __launch_bounds__(RES_THREADS, 1)
         for (int k = a_lo; k < a_hi; ++k)
           tma_load_2d(sB + (k % STAGES) * B_BYTES, &tmB, 0, brow, full_bar(k % STAGES));
         for (int k = a_hi - 1; k >= 0 && k >= a_hi - STAGES; --k)
-          (void)mbar_wait(full_bar(k % STAGES), (k / STAGES) & 1);
+          (void)mbar_wait(full_bar(k % STAGES), (k / STAGES) & 1, lim);
       }
     }
   } else if (warp == 1) {
@@ -166,8 +167,9 @@ __global__ void __launch_bounds__(RES_THREADS, 1)
     if (lane == 0) {
       constexpr uint32_t idesc = idesc_bf16<BN>();
       int it = 0;
+      int committed = -1;  // last step whose MMAs were committed to acc_full
       for (int n = 0; n < ra.steps; ++n) {
-        if (n > 0 && (!mbar_wait(acc_free, (n - 1) & 1) || *(volatile int*)&s_flag[0])) {
+        if (n > 0 && (!mbar_wait(acc_free, (n - 1) & 1, lim) || *(volatile int*)&s_flag[0])) {
           atomicOr(&s_flag[0], 1);
           break;
         }
@@ -176,7 +178,7 @@ __global__ void __launch_bounds__(RES_THREADS, 1)
         for (int kb = 0; kb < KB; ++kb, ++it) {
           const int s = it % STAGES;
           const uint32_t ph = (it / STAGES) & 1;
-          if (!mbar_wait(full_bar(s), ph) || *(volatile int*)&s_flag[0]) {
+          if (!mbar_wait(full_bar(s), ph, lim) || *(volatile int*)&s_flag[0]) {
             atomicOr(&s_flag[0], 1);
             stop = true;
             break;
@@ -191,8 +193,12 @@ __global__ void __launch_bounds__(RES_THREADS, 1)
         }
         if (n == 0) stamp(a, 3);
         mma_commit(acc_full);  // also after an abort: tracks every MMA issued
+        committed = n;
         if (stop) break;
       }
+      // after an abort, the MMAs still in flight finish before the CTA frees
+      // its tensor memory (the epilogue may have stopped waiting for them)
+      if (*(volatile int*)&s_flag[0] && committed >= 0) (void)mbar_wait(acc_full, committed & 1, lim);
     }
   } else {
     // ---------------- epilogue ----------------
@@ -272,15 +278,18 @@ __global__ void __launch_bounds__(RES_THREADS, 1)
     for (int n = 0; n < ra.steps; ++n) {
       sa.step = a.step + unsigned(n);
       sa.rho_in = (n & 1) ? ra.rho[1] : ra.rho[0];
+      bool flags_ok = true;
       if (e < RPT) {
         const int r = rbase + e;
         s_bstage[e] = s_beta[e];
         if (need_red && n > 0)  // partial sums of step n-1 from every row block of this column block
-          for (unsigned mb = 0; mb < gridDim.y; ++mb) (void)flag_wait(col_flags + mb, unsigned(n));
+          for (unsigned mb = 0; mb < gridDim.y && flags_ok; ++mb) flags_ok = flag_wait(col_flags + mb, unsigned(n), lim);
         s_dsc[e] = r < a.R ? noise_scale(sa, r) : 0.0f;
       }
-      epi_sync();
-      const bool ok = __all_sync(0xffffffffu, mbar_wait(acc_full, n & 1) && !*(volatile int*)&s_flag[0]);
+      // one decision for all epilogue warps (the vote is also the barrier that
+      // publishes s_bstage / s_dsc)
+      const bool ok =
+          epi_vote_all<32 * EPI_WARPS>(flags_ok && mbar_wait(acc_full, n & 1, lim) && !*(volatile int*)&s_flag[0]);
       tc_fence_after();
       if (!ok) {
         if (lane == 0) atomicOr(a.err, E_TIMEOUT);
@@ -377,9 +386,10 @@ __global__ void __launch_bounds__(RES_THREADS, 1)
         s_beta[e] = next_beta(sa, s_beta[e]);
       }
       epi_sync();
-      if (e == 0 && n + 1 < ra.steps) {
+      const int tile = int(blockIdx.x * gridDim.y + blockIdx.y);
+      if (e == 0 && n + 1 < ra.steps && !(tile == ra.withhold_tile && n + 1 == ra.withhold_step)) {
         __threadfence();
-        st_release_gpu(ra.flags + size_t(blockIdx.x) * gridDim.y + blockIdx.y, unsigned(n + 1));
+        st_release_gpu(ra.flags + tile, unsigned(n + 1));
       }
     }
     // tensor memory -> state

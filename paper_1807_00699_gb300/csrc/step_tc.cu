@@ -6,6 +6,9 @@ namespace gda {
 
 int tc_mtiles(int N) { return (N + BM - 1) / BM; }
 
+long long ptx_default_wait_cycles() { return kWaitCycles; }
+double ptx_cycles_per_second() { return kCyclesPerSecond; }
+
 // Two-SM pairs: a 256 x BN pair tile costs each SM about max(BN, 128 + BN / 2)
 // cycles per 16-deep K slice (MMA time against its shared-memory feed: own A
 // rows plus half of B), over ceil(pair tiles / clusters) rounds.

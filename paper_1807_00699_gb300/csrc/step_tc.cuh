@@ -79,6 +79,7 @@ __global__ void __launch_bounds__(TcThreads<MODE>::N, 1)
   int* s_flag = reinterpret_cast<int*>(s_tmem + 1);  // [0] abort, [1] diverged
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long lim = a.wait_cycles;
   constexpr int BKE = F8 ? 2 * BK : BK;  // elements per 128-byte K slice
   const int KB = (a.N + BKE - 1) / BKE;
   const int NT = (a.C + BN - 1) / BN;
@@ -132,7 +133,7 @@ __global__ void __launch_bounds__(TcThreads<MODE>::N, 1)
         for (int kb = 0; kb < KB; ++kb, ++it) {
           const int s = it % STAGES;
           const uint32_t ph = (it / STAGES) & 1;
-          if (!mbar_wait(empty_bar(s), ph ^ 1u) || *(volatile int*)&s_flag[0]) {
+          if (!mbar_wait(empty_bar(s), ph ^ 1u, lim) || *(volatile int*)&s_flag[0]) {
             stop = true;
             break;
           }
@@ -155,9 +156,9 @@ __global__ void __launch_bounds__(TcThreads<MODE>::N, 1)
         // stages to release them (bounded: the even CTA may have stopped)
         for (int k = it - 1; k >= 0 && k >= it - STAGES; --k) {
           if (!PAIR || leader)
-            (void)mbar_wait(full_bar(k % STAGES), (k / STAGES) & 1);
+            (void)mbar_wait(full_bar(k % STAGES), (k / STAGES) & 1, lim);
           else
-            (void)mbar_wait(empty_bar(k % STAGES), (k / STAGES) & 1);
+            (void)mbar_wait(empty_bar(k % STAGES), (k / STAGES) & 1, lim);
         }
       }
     }
@@ -171,7 +172,8 @@ __global__ void __launch_bounds__(TcThreads<MODE>::N, 1)
       for (int t = unit0; t < T && !stop; t += nunit, ++lt) {
         const int b = lt & 1;
         const uint32_t use = lt >> 1;
-        const bool free_ok = PAIR ? mbar_wait_cluster(acc_empty(b), (use & 1) ^ 1u) : mbar_wait(acc_empty(b), (use & 1) ^ 1u);
+        const bool free_ok = PAIR ? mbar_wait_cluster(acc_empty(b), (use & 1) ^ 1u, lim)
+                                  : mbar_wait(acc_empty(b), (use & 1) ^ 1u, lim);
         if (!free_ok || *(volatile int*)&s_flag[0]) {
           stop = true;
           break;
@@ -181,7 +183,7 @@ __global__ void __launch_bounds__(TcThreads<MODE>::N, 1)
         for (int kb = 0; kb < KB; ++kb, ++it) {
           const int s = it % STAGES;
           const uint32_t ph = (it / STAGES) & 1;
-          if (!mbar_wait(full_bar(s), ph) || *(volatile int*)&s_flag[0]) {
+          if (!mbar_wait(full_bar(s), ph, lim) || *(volatile int*)&s_flag[0]) {
             stop = true;
             break;
           }
@@ -214,7 +216,7 @@ __global__ void __launch_bounds__(TcThreads<MODE>::N, 1)
         else
           mma_commit(acc_full(b));
         if (stop) {
-          (void)mbar_wait(acc_full(b), use & 1);  // those MMAs finish before the CTA frees TMEM
+          (void)mbar_wait(acc_full(b), use & 1, lim);  // those MMAs finish before the CTA frees TMEM
           break;
         }
       }
@@ -256,8 +258,9 @@ __global__ void __launch_bounds__(TcThreads<MODE>::N, 1)
         s_beta[e] = stage_beta(a, bt);
         s_dsc[e] = r < a.R ? noise_scale(a, r) : 0.0f;
       }
-      epi_bar_sync_n<32 * NEPI>();
-      const bool ok = __all_sync(0xffffffffu, mbar_wait(acc_full(b), use & 1) && !*(volatile int*)&s_flag[0]);
+      // one decision for all epilogue warps (the vote is also the barrier that
+      // publishes s_beta / s_dsc)
+      const bool ok = epi_vote_all<32 * NEPI>(mbar_wait(acc_full(b), use & 1, lim) && !*(volatile int*)&s_flag[0]);
       tc_fence_after();
       if (!ok) {
         if (lane == 0) atomicOr(a.err, E_TIMEOUT);

@@ -11,7 +11,10 @@ namespace ptx {
 
 constexpr int BM = 128;  // MMA rows (tensor-memory lanes)
 constexpr int BK = 64;   // 64 BF16 = 128 bytes: one swizzle row
-constexpr long long kWaitCycles = 4000000000LL;  // about two seconds
+constexpr long long kWaitCycles = 4000000000LL;  // default wait limit: about two seconds
+// SM clock cycles per second used to turn a wait limit in seconds into
+// cycles (at least the GB300's highest SM clock, so a limit never ends early).
+constexpr double kCyclesPerSecond = 2.1e9;
 
 static __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -47,21 +50,23 @@ static __device__ __forceinline__ bool mbar_try_cluster(uint32_t bar, uint32_t p
   return ok != 0;
 }
 
-// Bounded wait for the phase with the given parity to complete.
-static __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+// Bounded wait for the phase with the given parity to complete: false once
+// `limit` SM clock cycles have passed without it.
+static __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long limit = kWaitCycles) {
   if (mbar_try(bar, parity)) return true;
   const long long t0 = clock64();
   while (!mbar_try(bar, parity)) {
-    if (clock64() - t0 > kWaitCycles) return false;
+    if (clock64() - t0 > limit) return false;
   }
   return true;
 }
 
-static __device__ __forceinline__ bool mbar_wait_cluster(uint32_t bar, uint32_t parity) {
+static __device__ __forceinline__ bool mbar_wait_cluster(uint32_t bar, uint32_t parity,
+                                                         long long limit = kWaitCycles) {
   if (mbar_try_cluster(bar, parity)) return true;
   const long long t0 = clock64();
   while (!mbar_try_cluster(bar, parity)) {
-    if (clock64() - t0 > kWaitCycles) return false;
+    if (clock64() - t0 > limit) return false;
   }
   return true;
 }
@@ -273,6 +278,24 @@ static __device__ __forceinline__ void epi_bar_sync() { asm volatile("bar.sync 1
 template <int N>
 static __device__ __forceinline__ void epi_bar_sync_n() {
   asm volatile("bar.sync 1, %0;" ::"n"(N) : "memory");
+}
+
+// Barrier over the N epilogue threads (named barrier 2) that also returns the
+// AND of every thread's predicate, so that all epilogue warps take the same
+// branch after a wait: a warp that leaves its loop alone would leave the
+// others waiting at a named barrier without a time limit.
+template <int N>
+static __device__ __forceinline__ bool epi_vote_all(bool p) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred q, o;\n\t"
+      "setp.ne.u32 q, %1, 0;\n\t"
+      "bar.red.and.pred o, 2, %2, q;\n\t"
+      "selp.u32 %0, 1, 0, o;\n\t}"
+      : "=r"(r)
+      : "r"(static_cast<uint32_t>(p)), "n"(N)
+      : "memory");
+  return r != 0;
 }
 
 

@@ -36,8 +36,8 @@ class Params(ct.Structure):
                 ("eps_hat", ct.c_double), ("noise_D", ct.c_double), ("noise_decay", ct.c_int32),
                 ("energy_every", ct.c_int32), ("seed", ct.c_uint64), ("init_mode", ct.c_int32),
                 ("schedule", ct.c_int32), ("init_amp", ct.c_double), ("coupling", ct.c_int32),
-                ("reserved", ct.c_int32), ("gamma_c", ct.c_double), ("q", ct.c_int32), ("reserved2", ct.c_int32),
-                ("hq", ct.c_double)]
+                ("withhold_flag", ct.c_int32), ("gamma_c", ct.c_double), ("q", ct.c_int32),
+                ("reserved2", ct.c_int32), ("hq", ct.c_double), ("wait_s", ct.c_double)]
 
 
 SIGNATURES = {
@@ -56,6 +56,7 @@ SIGNATURES = {
     "gda_best_seen": (ct.c_int, [_VP, _D, ct.POINTER(ct.c_int32), ct.POINTER(ct.c_int64), _VP]),
     "gda_trace": (ct.c_int, [_VP, ct.POINTER(ct.c_int64), _D, ct.POINTER(ct.c_int32), ct.c_int32,
                              ct.POINTER(ct.c_int32)]),
+    "gda_trace_energy": (ct.c_int, [_VP, ct.c_int32, ct.c_int32, _D]),
     "gda_coupling": (ct.c_int, [_VP, ct.c_int32, ct.c_int32, _F, _F]),
     "gda_profile": (ct.c_int, [_VP, ct.c_int32]),
     "gda_profile_read": (ct.c_int, [_VP, ct.POINTER(ct.c_uint64), ct.c_int32, ct.POINTER(ct.c_int32)]),
@@ -243,6 +244,15 @@ class Solver:
                                         _ptr(r, ct.c_int32), cap, ct.byref(n)))
         m = min(n.value, cap)
         return steps[:m], E[:m], r[:m]
+
+    def trace_energy(self, first: int = 0, count: int | None = None) -> np.ndarray:
+        """FP64 energies of the configurations the trace names (gda_trace_energy):
+        entry k is the lowest-tracked restart as it was at trace step k."""
+        if count is None:
+            count = len(self.trace()[0]) - first
+        E = np.empty(max(count, 0), dtype=np.float64)
+        self._check(self._lib.gda_trace_energy(self._h, int(first), int(count), _ptr(E, ct.c_double)))
+        return E
 
     def coupling(self, X: np.ndarray, prec: int = FP32) -> np.ndarray:
         """Y = J0 X (the coupling product alone) for X of shape (R, N)."""

@@ -45,7 +45,30 @@ def test_default_params(lib):
     p = gda.default_params()
     assert (p.dt, p.eps, p.rho_th, p.beta0, p.eps_hat, p.noise_D) == (0.01, 0.1, 1.0, 1.0, 0.0, 0.0)
     assert p.integ == gda.EULER and p.prec == gda.FP32 and p.init_mode == 1
-    assert ct.sizeof(gda.Params) == 128
+    assert ct.sizeof(gda.Params) == 136
+    assert p.wait_s == 0.0 and p.withhold_flag == 0
+
+
+def test_params_layout_matches_header(tmp_path):
+    """The ctypes mirror of gda_params has the header's size and field offsets
+    (checked by compiling the header with the host C compiler)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    names = [f[0] for f in gda.Params._fields_]
+    src = ["#include <stddef.h>", "#include <stdio.h>", f'#include "{os.path.join(ROOT, "include", "gda.h")}"',
+           "int main(void) {", '  printf("%zu\\n", sizeof(gda_params));']
+    src += [f'  printf("%zu\\n", offsetof(gda_params, {n}));' for n in names]
+    src += ["  return 0;", "}"]
+    c = tmp_path / "layout.c"
+    c.write_text("\n".join(src) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, str(c), "-o", str(exe)], check=True)
+    out = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert out[0] == ct.sizeof(gda.Params)
+    assert out[1:] == [getattr(gda.Params, n).offset for n in names]
 
 
 def test_status_strings(lib):

@@ -73,3 +73,49 @@ def test_best_seen_spans_continuations_and_resets(gda):
     _, _, st3, _ = s.best_seen()
     assert st3 <= 40
     s.close()
+
+
+@pytest.mark.parametrize("prec,sched", [("bf16", "resident"), ("bf16", "per_step"), ("fp32", "per_step")])
+def test_trace_energy_is_the_fp64_energy_of_the_named_restart(gda, prec, sched):
+    """gda_trace_energy: entry k is the FP64 Eq. (1) energy of the restart the
+    trace names at step k, as it was then.  Checked against segment-by-segment
+    continuations (bit-identical to one run) whose state is read back and
+    evaluated by the oracle."""
+    n, R, every, segs = 300, 96, 20, 5
+    J, g = synth.xy_gaussian(n, 31)
+    p = gda.BF16 if prec == "bf16" else gda.FP32
+    sc = {"resident": gda.RESIDENT, "per_step": gda.PER_STEP}[sched]
+    kw = dict(dt=0.05, eps=0.1, prec=p, schedule=sc, energy_every=every, seed=17, noise_D=0.01)
+    s = gda.Solver(J, g, gda.XY)
+    s.run(gda.default_params(**kw), R, every * segs)
+    steps, Et, rs = s.trace()
+    E64 = s.trace_energy()
+    assert len(E64) == segs and list(steps) == [every * (k + 1) for k in range(segs)]
+    with pytest.raises(gda.GdaError):
+        s.trace_energy(0, segs + 1)
+    s2 = gda.Solver(J, g, gda.XY)
+    for k in range(segs):
+        s2.run(gda.default_params(**dict(kw, init_mode=1 if k == 0 else 2)), R, every)
+        st2, Et2, rs2 = s2.trace()
+        assert st2[0] == steps[k] and rs2[0] == rs[k] and Et2[0] == Et[k]
+        psi = s2.get_state()[0]
+        ref = oracle.energies(J, g, oracle.project(psi[rs[k]][None].astype(np.complex128)))[0]
+        assert E64[k] == pytest.approx(ref, rel=1e-9, abs=1e-9), k
+        assert s2.trace_energy()[0] == E64[k]
+        # the tracked value approximates the FP64 one (BF16 operands: ~1e-3)
+        assert Et[k] == pytest.approx(E64[k], rel=2e-3 if prec == "bf16" else 1e-4)
+    s.close()
+    s2.close()
+
+
+def test_trace_energy_exact_for_integer_ising(gda):
+    n, R = 20, 64
+    J, g = synth.ising_pm1(n, 4)
+    s = gda.Solver(J, g, gda.ISING)
+    s.run(gda.default_params(dt=0.01, eps=0.1, energy_every=50, seed=3), R, 500)
+    E64 = s.trace_energy()
+    assert len(E64) == 10 and np.all(E64 == np.round(E64))
+    # the last entry is the final state of the restart it names
+    r_last = s.trace()[2][-1]
+    assert E64[-1] == s.energy()[r_last]
+    s.close()
