@@ -1,15 +1,20 @@
-"""Benchmark of the GD hot path on synthetic XY instances shaped like the
-paper's dense random couplings.
+"""Benchmark of the GD hot path on synthetic instances shaped like the paper's
+dense random couplings.
 
-Workload (one bench step = one full solve): XY model, N = 1000 spins with
-J_ij ~ N(0, 1/N) (symmetric, zero diagonal), g_i ~ U[-0.1, 0.1], R = 1024
-restarts, 5000 GD steps (Eqs. 2, 5; forward Euler, dt = 0.05, eps = 0.1,
-rho_th = 1, seeded U(-1e-3, 1e-3) start), tracking energy every 100 steps,
-then the FP64 Eq. (1) energies of all restarts and the argmin.
+Default workload (one bench step = one full solve): Ising model on a
+Sherrington-Kirkpatrick instance, N = 4096 spins, J_ij ~ N(0, 1) (symmetric,
+zero diagonal), g = 0, R = 4096 restarts, 10000 forward-Euler GD steps of
+Eqs. (2), (5), (6) with the coupling ramp (dt = 0.1 / sqrt(N), eps = 0.03,
+rho_th = 1, beta0 = 0.5, eps_hat = 0.05, seeded U(-1e-3, 1e-3) start), BF16
+coupling product on tensor cores, tracking energy every 100 steps, then the
+lowest FP64 Eq. (1) energy over the restarts.  `--workload xy1000` runs the
+XY N = 1000, R = 1024, 5000-step workload instead.
 
 Metric: spin-updates/s = N R steps / time (one update = one spin of one
-restart advanced by one step), plus the time to reach the target energy
-(within 1e-3 relative of the best FP64-verified energy of any variant).
+restart advanced by one step), plus the time to reach the target energy: the
+first trace point at which the configuration the trace names (the restart
+with the lowest tracking energy, as it was then) has an FP64 energy within
+1e-3 relative of the best FP64-verified energy of any arm.
 """
 from __future__ import annotations
 
@@ -27,9 +32,19 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
-WORKLOAD = dict(name="xy_dense_gaussian_N1000_R1024_5000steps", model="xy", N=1000, R=1024, steps=5000,
-                dt=0.05, eps=0.1, rho_th=1.0, init_amp=1e-3, energy_every=100, seed=1)
+WORKLOADS = {
+    "sk4096": dict(name="ising_sk_gaussian_N4096_R4096_10000steps_ramp", model="ising", N=4096, R=4096,
+                   steps=10000, dt=0.1 / 64.0, eps=0.03, rho_th=1.0, beta0=0.5, eps_hat=0.05, init_amp=1e-3,
+                   energy_every=100, seed=100, inst_seed=0),
+    "xy1000": dict(name="xy_dense_gaussian_N1000_R1024_5000steps", model="xy", N=1000, R=1024, steps=5000,
+                   dt=0.05, eps=0.1, rho_th=1.0, beta0=1.0, eps_hat=0.0, init_amp=1e-3, energy_every=100, seed=1,
+                   inst_seed=1),
+}
 METRIC = "time-to-target energy (s) & spin-updates/s: BF16+learned vs plain FP32 GDA"
+# DRAM bytes (read + write) per launch of each workload's dominant kernel, from
+# one-launch ncu captures (profiles/): None where no capture of the current
+# kernel exists.
+TRAFFIC = {"sk4096": None, "xy1000": None}
 
 
 def parse():
@@ -40,11 +55,12 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="bf16", choices=["bf16", "fp32", "fp8", "sparse"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-fp32-ttt", action="store_true")
-    ap.add_argument("--workload", default="xy1000", choices=["xy1000", "batched", "sk4096", "kernel"],
-                    help="xy1000: the headline workload; batched: the 2000-instance serving mix; "
-                         "sk4096: SK N=4096 R=4096 quality per precision (FP32 / BF16 / FP8); "
-                         "kernel: time per step of one configuration (the small cases profiled with ncu)")
+    ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-target arms")
+    ap.add_argument("--workload", default="sk4096",
+                    choices=["sk4096", "xy1000", "batched", "sk_quality", "kernel"],
+                    help="sk4096: the headline workload (Ising SK N = R = 4096, 10000 steps); xy1000: XY N = 1000, "
+                         "R = 1024, 5000 steps; batched: the 2000-instance serving mix; sk_quality: SK N = R = 4096 "
+                         "quality per precision over several seeds; kernel: time per step of one configuration")
     ap.add_argument("--model", default="xy", choices=["xy", "ising", "ising3r"],
                     help="kernel workload: XY (J ~ N(0, 1/N)), Ising SK (J ~ N(0, 1)) or Ising on the paper's "
                          "sparse 3-regular graphs (weights U[a, b], a, b in {-10, -3, 3, 10})")
@@ -56,7 +72,7 @@ def parse():
                     help="kernel workload: GD (K = beta J) or GD-mod (per-restart K, FP32)")
     ap.add_argument("--kernel-steps", type=int, default=20, help="kernel workload: timed steps")
     ap.add_argument("--timeline", action="store_true", help="kernel workload: per-CTA device timestamps")
-    ap.add_argument("--sk-seeds", default="0", help="comma-separated instance seeds of the sk4096 workload")
+    ap.add_argument("--sk-seeds", default="0", help="comma-separated instance seeds of the sk_quality workload")
     ap.add_argument("--batch-count", type=int, default=2000)
     return ap.parse_args()
 
@@ -65,10 +81,18 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
-def instance():
+def instance(W):
     import synth
-    J, g = synth.xy_gaussian(WORKLOAD["N"], WORKLOAD["seed"])
-    return J, g
+    if W["model"] == "xy":
+        return synth.xy_gaussian(W["N"], W["inst_seed"])
+    return synth.sk_gaussian(W["N"], W["inst_seed"])
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
 
 
 # ---------------------------------------------------------------- clocks
@@ -117,50 +141,205 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- oracle arm
-def oracle_sample(budget_s: float = 12.0):
+def oracle_sample(W, budget_s: float = 12.0):
     """The CPU oracle as it stands on a bounded sample of the workload: the
-    same instance, R = 64 restarts, as many steps as fit in ~budget_s."""
+    same instance and settings, a subset of the restarts, as many steps as fit
+    in about budget_s seconds."""
     import oracle
-    J, g = instance()
-    W = WORKLOAD
-    R = 64
-    p = oracle.Params(dt=W["dt"], eps=W["eps"], rho_th=W["rho_th"], init_amp=W["init_amp"], seed=W["seed"])
+    J, g = instance(W)
+    R = 16 if W["N"] > 2000 else 64
+    p = oracle.Params(dt=W["dt"], eps=W["eps"], rho_th=W["rho_th"], beta0=W["beta0"], eps_hat=W["eps_hat"],
+                      init_amp=W["init_amp"], seed=W["seed"])
     t0 = time.perf_counter()
     state = None
     steps = 0
     while True:
-        state = oracle.run(J, g, "xy", p, R, 10, state=state, step0=steps)
+        state = oracle.run(J, g, W["model"], p, R, 10, state=state, step0=steps)
         steps += 10
         if time.perf_counter() - t0 > budget_s or steps >= W["steps"]:
             break
     dt = time.perf_counter() - t0
     return {"value": W["N"] * R * steps / dt, "unit": "spin-updates/s", "cores": os.cpu_count(),
-            "kind": "oracle", "sample": f"XY N={W['N']}, R={R} restarts, {steps} FP64 Euler steps "
-                                         f"(numpy, default BLAS threads) in {dt:.1f} s"}
+            "kind": "oracle", "seconds": dt,
+            "sample": f"{W['model']} N={W['N']}, R={R} restarts, {steps} FP64 Euler steps of the workload's "
+                      f"instance and settings (numpy, default BLAS threads) in {dt:.1f} s"}
+
+
+def workload_config(W, world=1):
+    return {"workload": W["name"], "model": W["model"], "N": W["N"], "R": W["R"], "steps": W["steps"],
+            "integrator": "euler", "dt": W["dt"], "eps": W["eps"], "beta0": W["beta0"], "eps_hat": W["eps_hat"],
+            "energy_every": W["energy_every"], "l2": "flushed (256 MB write) between timed steps",
+            "parallelism": f"replicas{world}"}
 
 
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    vals = []
+    W = WORKLOADS[args.workload if args.workload in WORKLOADS else "sk4096"]
     for _ in range(args.warmup):
-        oracle_sample(2.0)
-    for _ in range(args.steps):
-        vals.append(oracle_sample(8.0))
+        oracle_sample(W, 1.0)
+    vals = [oracle_sample(W, 6.0) for _ in range(args.steps)]
     v = float(np.median([x["value"] for x in vals]))
     cpu = dict(vals[-1])
     cpu["value"] = v
-    W = WORKLOAD
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "spin-updates/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * W["N"] * W["R"] * W["steps"] / v, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": W["name"], "N": W["N"], "R": W["R"], "steps": W["steps"],
-                       "integrator": "euler", "sample": cpu["sample"]},
+            # one bench step of this arm is one bounded sample: its measured wall time
+            "ms_per_step": 1e3 * float(np.mean([x["seconds"] for x in vals])),
+            # the full solve of the workload at the sample's rate (an extrapolation)
+            "ms_per_solve_extrapolated": 1e3 * W["N"] * W["R"] * W["steps"] / v,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(workload_config(W, world), sample=cpu["sample"]),
             "cpu_baseline": cpu,
             "e2e": {"value": v, "unit": "spin-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- time to target
+def gd_params(gda, W, **over):
+    kw = dict(dt=W["dt"], eps=W["eps"], rho_th=W["rho_th"], beta0=W["beta0"], eps_hat=W["eps_hat"], init_mode=1,
+              init_amp=W["init_amp"], seed=W["seed"], energy_every=W["energy_every"])
+    kw.update(over)
+    return gda.default_params(**kw)
+
+
+def ttt_arm(torch, stream, solver, params, R, steps, pre=None):
+    """One time-to-target arm: `steps` steps with the energy trace, timed with
+    CUDA events on the solver's stream (pre: an optional set-up inside the
+    timed region, e.g. the learned proposal, returning the run parameters).
+    After the timed region: the FP64 energies of the configurations the trace
+    names (gda_trace_energy) and of every restart at the end."""
+    e0, ep, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    torch.cuda.synchronize()
+    e0.record(stream)
+    extra = None
+    if pre is not None:
+        params, extra = pre()
+    ep.record(stream)
+    solver.run(params, R, steps)
+    e1.record(stream)
+    e1.synchronize()
+    st, Et, rt = solver.trace()
+    return {"t_pre": e0.elapsed_time(ep) / 1e3, "t_run": ep.elapsed_time(e1) / 1e3, "steps": st, "Et": Et,
+            "E64": solver.trace_energy(), "E_all": solver.energy(), "total_steps": steps, "extra": extra}
+
+
+def score_arms(arms: dict, base: str) -> dict:
+    """E* = the best FP64-verified energy of any arm (final restarts and every
+    traced configuration); target = E* + 1e-3 |E*|; an arm's time to target is
+    its proposal time plus the run time up to the first trace point whose named
+    configuration has an FP64 energy at or below the target (the run time is
+    prorated by steps: every step of a run costs the same)."""
+    Estar = min(min(float(a["E_all"].min()), float(a["E64"].min()) if len(a["E64"]) else np.inf)
+                for a in arms.values())
+    target = Estar + 1e-3 * abs(Estar)
+    out = {"E_star_fp64": Estar, "target_E": target}
+    for name, a in arms.items():
+        hit = np.nonzero(a["E64"] <= target)[0]
+        k = int(hit[0]) if len(hit) else None
+        steps_hit = None if k is None else int(a["steps"][k])
+        row = {"ttt_s": None if k is None else a["t_pre"] + steps_hit / a["total_steps"] * a["t_run"],
+               "steps_to_target": steps_hit, "run_s": a["t_pre"] + a["t_run"], "steps": a["total_steps"],
+               # the FP64 energy of the configuration at the hit (<= target by construction)
+               "E_fp64_at_hit": None if k is None else float(a["E64"][k]),
+               "E_tracked_at_hit": None if k is None else float(a["Et"][k]),
+               # first trace point whose tracking energy alone was at or below the target
+               "steps_tracking_only": (None if not np.any(a["Et"] <= target)
+                                       else int(a["steps"][np.nonzero(a["Et"] <= target)[0][0]])),
+               "E_best_fp64_final": float(a["E_all"].min()), "E_best_fp64_traced": float(a["E64"].min()),
+               "gap_rel": (float(a["E_all"].min()) - Estar) / abs(Estar),
+               "success_prob": float(np.mean(a["E_all"] <= target))}
+        if a["extra"] is not None:
+            row.update({"proposal_s": a["t_pre"], "settings": a["extra"]})
+        out[name] = row
+    b = out[base]
+    for name in arms:
+        if name == base or out[name]["ttt_s"] is None:
+            continue
+        if b["ttt_s"]:
+            out[f"speedup_{name}_vs_{base}"] = b["ttt_s"] / out[name]["ttt_s"]
+        else:  # the base never reached the target within its run: a lower bound
+            out[f"speedup_{name}_vs_{base}_lower_bound"] = b["run_s"] / out[name]["ttt_s"]
+    return out
+
+
+def ttt_precisions(gda, torch, stream, W, J, g, model):
+    """The headline instance and settings through the plain FP32, BF16 and FP8
+    coupling products: same start, same steps (precision is the only factor)."""
+    arms = {}
+    for name, prec in (("fp32_plain", gda.FP32), ("bf16_plain", gda.BF16), ("fp8_plain", gda.FP8)):
+        s = gda.Solver(J, g, model, stream=stream)
+        s.run(gd_params(gda, W, prec=prec, energy_every=0), W["R"], 3)  # warm-up
+        arms[name] = ttt_arm(torch, stream, s, gd_params(gda, W, prec=prec), W["R"], W["steps"])
+        s.close()
+    out = score_arms(arms, "fp32_plain")
+    out["instance"] = W["name"]
+    return out
+
+
+def ttt_settings(gda, torch, stream):
+    """XY N = 1000 (J ~ N(0, 1/N), g ~ U[-0.1, 0.1]), R = 1024, 20000 steps:
+    the plain algorithm at its default settings, at the best fixed setting of
+    the proposal's grid (chosen on two other seeded instances), and with the
+    learned proposal (settings and start), in FP32 and BF16; each factor is
+    varied alone against an arm that shares the rest."""
+    import synth
+    from paper_1807_00699_gb300 import proposal
+    W = dict(WORKLOADS["xy1000"])
+    steps, R = 4 * W["steps"], W["R"]
+    J, g = instance(W)
+    base = dict(dt=W["dt"], init_amp=W["init_amp"], seed=W["seed"], energy_every=W["energy_every"])
+
+    # best fixed grid setting: calibrated on two other instances of the same family
+    calib = {}
+    for cs in (2001, 2002):
+        Jc, gc = synth.xy_gaussian(W["N"], cs)
+        s = gda.Solver(Jc, gc, gda.XY, stream=stream)
+        runs = {}
+        for k, (e, rho, b0) in enumerate(proposal.GRID):
+            prm = proposal.run_params({"eps": e, "rho_th": rho, "beta0": b0}, init_mode=1, prec=gda.BF16, **base)
+            runs[k] = ttt_arm(torch, stream, s, prm, R, steps)
+        sc = score_arms(runs, 0)
+        for k in runs:
+            st = sc[k]["steps_to_target"]
+            calib.setdefault(k, []).append(st if st is not None else 10 ** 9)
+        s.close()
+    k_fixed = min(calib, key=lambda k: (sum(x >= 10 ** 9 for x in calib[k]), float(np.mean(calib[k]))))
+    fixed = dict(zip(("eps", "rho_th", "beta0"), proposal.GRID[k_fixed]))
+
+    prop = proposal.Proposal()
+    s = gda.Solver(J, g, gda.XY, stream=stream)
+    s32 = gda.Solver(J, g, gda.XY, stream=stream)
+    plain = dict(eps=W["eps"], rho_th=W["rho_th"], beta0=W["beta0"], eps_hat=W["eps_hat"])
+    s.run(gda.default_params(prec=gda.BF16, **dict(base, energy_every=0)), R, 3)
+    arms = {}
+    arms["fp32_plain"] = ttt_arm(torch, stream, s32, gda.default_params(prec=gda.FP32, init_mode=1, **plain, **base),
+                                 R, steps)
+    arms["bf16_plain"] = ttt_arm(torch, stream, s, gda.default_params(prec=gda.BF16, init_mode=1, **plain, **base),
+                                 R, steps)
+    arms["bf16_best_fixed"] = ttt_arm(torch, stream, s, proposal.run_params(fixed, init_mode=1, prec=gda.BF16, **base),
+                                      R, steps)
+
+    def learned(solver, prec):
+        def pre():
+            st = prop.propose(solver)
+            return proposal.proposed_params(st, W["seed"], dt=W["dt"], prec=prec,
+                                            energy_every=W["energy_every"]), st
+        return pre
+
+    arms["bf16_learned"] = ttt_arm(torch, stream, s, None, R, steps, pre=learned(s, gda.BF16))
+    arms["fp32_learned"] = ttt_arm(torch, stream, s32, None, R, steps, pre=learned(s32, gda.FP32))
+    s.close()
+    s32.close()
+    out = score_arms(arms, "fp32_plain")
+    out["instance"] = "xy_dense_gaussian_N1000_R1024_20000steps"
+    out["best_fixed_setting"] = {**fixed, "grid_index": k_fixed, "calibration_steps_to_target": calib[k_fixed]}
+    for name in ("bf16_learned",):
+        for ref in ("bf16_best_fixed", "bf16_plain"):
+            if out[name]["ttt_s"] and out[ref]["ttt_s"]:
+                out[f"speedup_{name}_vs_{ref}"] = out[ref]["ttt_s"] / out[name]["ttt_s"]
+    return out
 
 
 # ---------------------------------------------------------------- our arm
@@ -179,18 +358,17 @@ def run_ours(args):
         dist.barrier()
     from paper_1807_00699_gb300 import gda
 
-    W = WORKLOAD
-    J, g = instance()
+    W = WORKLOADS[args.workload]
+    J, g = instance(W)
+    model = gda.XY if W["model"] == "xy" else gda.ISING
     if args.prec == "sparse":
-        raise SystemExit("the headline XY instance is dense: time the sparse product with "
+        raise SystemExit("the headline instances are dense: time the sparse product with "
                          "--workload kernel --model ising3r --prec sparse")
     prec = {"fp32": gda.FP32, "bf16": gda.BF16, "fp8": gda.FP8}[args.prec]
     stream = torch.cuda.Stream()
-    s = gda.Solver(J, g, gda.XY, stream=stream)
+    s = gda.Solver(J, g, model, stream=stream)
     seed = W["seed"] + 1000 * rank  # ranks run independent restart sets (weak scaling)
-    sched = gda.RESIDENT if prec == gda.BF16 else gda.AUTO
-    p = gda.default_params(dt=W["dt"], eps=W["eps"], rho_th=W["rho_th"], init_mode=1, init_amp=W["init_amp"],
-                           seed=seed, energy_every=W["energy_every"], prec=prec, schedule=sched)
+    p = gd_params(gda, W, prec=prec, seed=seed)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
 
     def solve():
@@ -227,57 +405,50 @@ def run_ours(args):
         t_step = float(tt.item())
     units = W["N"] * W["R"] * W["steps"] * world
     value = units / t_step
-    steps_tr, E_tr, _ = s.trace()
     E_ours = Ebest
     if world > 1:
         from paper_1807_00699_gb300.replicas import combine_best
         E_ours = combine_best(Ebest, rbest)[0]  # best answer over the replicas
 
-    # dominant kernel alone: the step kernel, no tracking, timed on its stream
-    p_k = gda.default_params(dt=W["dt"], eps=W["eps"], rho_th=W["rho_th"], init_mode=1,
-                             init_amp=W["init_amp"], seed=seed, energy_every=0, prec=prec, schedule=sched)
-    s.run(p_k, W["R"], 50)
+    # dominant kernel alone: the step kernel (no tracking), CUDA events on its stream
+    s.run(gd_params(gda, W, prec=prec, seed=seed, energy_every=0), W["R"], 20)
     torch.cuda.synchronize()
+    nk = 1000 if W["N"] * W["R"] <= 2 ** 21 else 200
     k0 = torch.cuda.Event(enable_timing=True)
     k1 = torch.cuda.Event(enable_timing=True)
-    nk = 1000
     k0.record(stream)
-    s.run(gda.default_params(dt=W["dt"], eps=W["eps"], rho_th=W["rho_th"], init_mode=2, energy_every=0,
-                             prec=prec, schedule=sched), W["R"], nk)
+    s.run(gd_params(gda, W, prec=prec, seed=seed, energy_every=0, init_mode=2), W["R"], nk)
     k1.record(stream)
     k1.synchronize()
     t_kernel = k0.elapsed_time(k1) / 1e3 / nk
-    flops = 2.0 * W["N"] * W["N"] * 2 * W["R"]
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
+    flops = 2.0 * W["N"] * W["N"] * W["R"] * (2 if W["model"] == "xy" else 1)
+    peaks = load_peaks()
+    # a solve runs for seconds: the sustained tensor peak is the denominator
     if prec == gda.BF16:
-        peak = peaks.get("bf16_tflops", 1900.0)
-        src = "measured bf16 burst" if "bf16_tflops" in peaks else "fallback"
+        peak = peaks.get("bf16_tflops_sustained", 1700.0)
+        src = "measured bf16 sustained" if "bf16_tflops_sustained" in peaks else "fallback (sustained)"
     elif prec == gda.FP8:
-        peak = 2.0 * peaks.get("bf16_tflops", 1900.0)
-        src = ("measured bf16 burst x 2 (nominal fp8 / bf16 ratio)" if "bf16_tflops" in peaks
+        peak = 2.0 * peaks.get("bf16_tflops_sustained", 1700.0)
+        src = ("measured bf16 sustained x 2 (nominal fp8 / bf16 ratio)" if "bf16_tflops_sustained" in peaks
                else "fallback x 2")
     else:
         peak = 152 * 128 * 2 * 2.07e9 / 1e12
         src = "nominal FP32 CUDA-core rate (152 SMs x 128 FMA x 2.07 GHz)"
     achieved = flops / t_kernel / 1e12
-    kname = {gda.BF16: "step_res_kernel (resident: GEMM + fused epilogue, state in TMEM), time per step",
-             gda.FP8: "step_tc_kernel (per-step, E4M3 operands), time per step",
-             gda.FP32: "step_simt_kernel"}[prec]
-    # DRAM bytes per step of the resident kernel from the committed ncu capture of an
-    # 8-step launch (19.08 MB read + 0.04 MB written, all of it the cold start of the
-    # launch: J, state; HBM is idle in steady state)
-    traffic = (19.076e6 + 0.039e6) / 8 if prec == gda.BF16 else None
+    resident = W["model"] == "xy" and prec == gda.BF16
+    kname = ("step_res_kernel (resident: GEMM + fused epilogue, state in tensor memory), time per step" if resident
+             else {gda.BF16: "step_tc_kernel (per step, two-SM tiles at this size: GEMM + fused epilogue), time per step",
+                   gda.FP8: "step_tc_kernel (per step, E4M3 operands), time per step",
+                   gda.FP32: "step_simt_kernel"}[prec])
+    traffic = TRAFFIC.get(args.workload) if prec == gda.BF16 else None
     roofline = {"bound": "alu" if prec == gda.FP32 else "tensor", "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic, "kernel": kname,
-                "peak_source": src, "us_per_launch": t_kernel * 1e6}
+                "peak_source": src, "us_per_launch": t_kernel * 1e6, "flop_per_launch": flops,
+                "launches_timed": nk}
 
-    # end to end through host buffers: load J, solve, read the best configuration back
+    # end to end through host buffers: load J and g, solve, read the best configuration back
     e2e_times = []
-    for _ in range(max(1, args.steps)):
+    for _ in range(max(1, min(args.steps, 5))):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         s.load(J, g)
@@ -286,118 +457,30 @@ def run_ours(args):
         e2e_times.append(time.perf_counter() - t0)
     e2e_t = float(np.mean(e2e_times))
     h2d = W["N"] * W["N"] * 8 + W["N"] * 8
-    d2h = 8 + 4 + W["N"] * 8
+    d2h = 8 + 4 + W["N"] * (8 if W["model"] == "xy" else 1)
+    s.close()
 
-    # time to target: three arms on the same instance and start, each run for TTT_STEPS steps
-    # with the energy trace every 100 steps; E* = the best FP64-verified energy of any run,
-    # target = E* + 1e-3 |E*|; an arm's time to target = (first traced step at or below the
-    # target) / TTT_STEPS x its timed run (plus the proposal's own time for the learned arm)
     ttt = None
-    if rank == 0 and not args.no_fp32_ttt:
-        TTT_STEPS = 4 * W["steps"]
-
-        def timed_arm(solver, params, pre=None):
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            ep = torch.cuda.Event(enable_timing=True)
-            torch.cuda.synchronize()
-            e0.record(stream)
-            extra = pre() if pre else None
-            ep.record(stream)
-            solver.run(params if not callable(params) else params(extra), W["R"], TTT_STEPS)
-            E, _, _ = solver.best(with_cfg=False)
-            e1.record(stream)
-            e1.synchronize()
-            st, Et, _ = solver.trace()
-            # after the timed region: FP64 energies of every restart, and the running
-            # best of the trace (the configuration kept at the lowest tracked energy) in FP64
-            E_all = solver.energy()
-            E_seen, _, step_seen, _ = solver.best_seen(with_cfg=False)
-            return {"E": E, "steps": st, "Et": Et, "t": e0.elapsed_time(e1) / 1e3, "t_pre": e0.elapsed_time(ep) / 1e3,
-                    "extra": extra, "E_all": E_all, "E_seen": E_seen, "step_seen": step_seen}
-
-        s32 = gda.Solver(J, g, gda.XY, stream=stream)
-        arms = {"fp32_plain": timed_arm(s32, gda.default_params(
-            dt=W["dt"], eps=W["eps"], rho_th=W["rho_th"], init_mode=1, init_amp=W["init_amp"], seed=seed,
-            energy_every=W["energy_every"], prec=gda.FP32))}
-        s32.close()
-        arms["bf16_plain"] = timed_arm(s, gda.default_params(
-            dt=W["dt"], eps=W["eps"], rho_th=W["rho_th"], init_mode=1, init_amp=W["init_amp"], seed=seed,
-            energy_every=W["energy_every"], prec=prec, schedule=sched))
-        # BF16 + learned proposal (network settings and start); the proposal's own
-        # cost (features and forward pass) is inside the timed region
+    if rank == 0 and not args.no_ttt:
+        ttt = {"precisions": ttt_precisions(gda, torch, stream, W, J, g, model)}
         try:
-            from paper_1807_00699_gb300 import proposal
-            prop = proposal.Proposal()
-        except (OSError, RuntimeError):
-            prop = None
-        if prop is not None:
-            arms["bf16_learned"] = timed_arm(
-                s, lambda st: proposal.proposed_params(st, seed, dt=W["dt"], prec=prec, energy_every=W["energy_every"],
-                                                       schedule=sched),
-                pre=lambda: prop.propose(s))
-        Estar = min([E_ours] + [a["E"] for a in arms.values()] + [a["E_seen"] for a in arms.values()])
-        target = Estar + 1e-3 * abs(Estar)
-        ttt = {"target_E": target, "E_star_fp64": Estar, "steps_per_arm": TTT_STEPS,
-               "E_best_ours_5000_steps": E_ours}
-        for name, a in arms.items():
-            hit = np.nonzero(a["Et"] <= target)[0]
-            run_t = a["t"] - a["t_pre"]
-            t_hit = None if len(hit) == 0 else a["t_pre"] + float(a["steps"][hit[0]]) / TTT_STEPS * run_t
-            ttt[name] = {"E_best_fp64": a["E"], "ttt_s": t_hit, "run_s": a["t"],
-                         "steps_to_target": None if len(hit) == 0 else int(a["steps"][hit[0]]),
-                         # share of restarts whose final FP64 energy is within 1e-3 of E*
-                         "success_prob": float(np.mean(a["E_all"] <= target)),
-                         "gap_rel": (a["E"] - Estar) / abs(Estar),
-                         # the kept configuration of the lowest tracked energy, in FP64
-                         "best_seen_fp64": a["E_seen"], "best_seen_step": a["step_seen"],
-                         "target_verified_fp64": bool(a["E_seen"] <= target)}
-            if name == "bf16_learned":
-                ttt[name].update({"proposal_s": a["t_pre"], "settings": a["extra"]})
-        base = ttt["fp32_plain"]
-        for name in ("bf16_plain", "bf16_learned"):
-            if name in ttt and ttt[name]["ttt_s"]:
-                if base["ttt_s"]:
-                    ttt[f"speedup_{name}_vs_fp32_plain"] = base["ttt_s"] / ttt[name]["ttt_s"]
-                else:  # FP32 never reached the target within its run: a lower bound
-                    ttt[f"speedup_{name}_vs_fp32_plain_lower_bound"] = base["run_s"] / ttt[name]["ttt_s"]
-
-    # the paper's XY integrator: classical RK4 on the same instance and start
-    # (per-step launches, four stages per step; one RK4 step counts once)
-    rk4 = None
-    if rank == 0 and prec != gda.FP32:
-        p4 = gda.default_params(dt=W["dt"], eps=W["eps"], rho_th=W["rho_th"], init_mode=1, init_amp=W["init_amp"],
-                                seed=seed, energy_every=W["energy_every"], prec=prec, integ=gda.RK4)
-        s.run(p4, W["R"], 20)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        s.run(p4, W["R"], W["steps"])
-        E4, _, _ = s.best(with_cfg=False)
-        e1.record(stream)
-        e1.synchronize()
-        t4 = e0.elapsed_time(e1) / 1e3
-        rk4 = {"solve_s": t4, "spin_updates_per_s": W["N"] * W["R"] * W["steps"] / t4, "E_best_fp64": E4,
-               "ms_per_step": t4 / W["steps"] * 1e3, "schedule": "per-step (4 launches per step)"}
+            ttt["settings_xy1000"] = ttt_settings(gda, torch, stream)
+        except (OSError, RuntimeError) as exc:  # no trained proposal parameters
+            ttt["settings_xy1000"] = {"unavailable": str(exc)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = oracle_sample(12.0)
+        cpu = oracle_sample(W, 12.0)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "spin-updates/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": {gda.BF16: "bf16", gda.FP8: "fp8_e4m3", gda.FP32: "f32"}[prec], "data": "synthetic",
-                "config": {"workload": W["name"], "model": "xy", "N": W["N"], "R": W["R"], "steps": W["steps"],
-                           "integrator": "euler", "dt": W["dt"], "energy_every": W["energy_every"],
-                           "l2": "flushed (256 MB write) between timed steps", "parallelism": f"replicas{world}"},
-                "time_to_target": ttt, "rk4": rk4, "clocks": clocks.summary(), "roofline": roofline,
-                "cpu_baseline": cpu,
+                "vs_baseline": None, "dtype": {gda.BF16: "bf16", gda.FP8: "fp8_e4m3", gda.FP32: "f32"}[prec],
+                "data": "synthetic", "config": workload_config(W, world), "E_best_fp64": E_ours,
+                "time_to_target": ttt, "clocks": clocks.summary(), "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": {"value": units / e2e_t, "unit": "spin-updates/s", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
                 "gpu_launches": int(launches)}
         print(json.dumps(line), flush=True)
-    s.close()
     if world > 1:
         dist.destroy_process_group()
 
@@ -644,7 +727,7 @@ def main():
         run_reference(args)
     elif args.workload == "batched":
         run_batched(args)
-    elif args.workload == "sk4096":
+    elif args.workload == "sk_quality":
         run_sk(args)
     elif args.workload == "kernel":
         run_kernel(args)
