@@ -286,6 +286,9 @@ static __device__ __forceinline__ void epi_bar_sync_n() {
 // others waiting at a named barrier without a time limit.
 template <int N>
 static __device__ __forceinline__ bool epi_vote_all(bool p) {
+  // the warp agrees first (and is converged for the aligned barrier)
+  p = __all_sync(0xffffffffu, p);
+  __syncwarp();
   uint32_t r;
   asm volatile(
       "{\n\t.reg .pred q, o;\n\t"
