@@ -330,16 +330,64 @@ def ttt_settings(gda, torch, stream):
 
     arms["bf16_learned"] = ttt_arm(torch, stream, s, None, R, steps, pre=learned(s, gda.BF16))
     arms["fp32_learned"] = ttt_arm(torch, stream, s32, None, R, steps, pre=learned(s32, gda.FP32))
-    s.close()
-    s32.close()
     out = score_arms(arms, "fp32_plain")
     out["instance"] = "xy_dense_gaussian_N1000_R1024_20000steps"
+    k_hit = out["bf16_learned"]["steps_to_target"]
+    if k_hit:
+        out["bf16_batched_learned"] = batched_learned_arm(gda, torch, stream, prop, s, J, g, W, R, k_hit,
+                                                         out["bf16_learned"]["proposal_s"])
+    s.close()
+    s32.close()
     out["best_fixed_setting"] = {**fixed, "grid_index": k_fixed, "calibration_steps_to_target": calib[k_fixed]}
-    for name in ("bf16_learned",):
-        for ref in ("bf16_best_fixed", "bf16_plain"):
-            if out[name]["ttt_s"] and out[ref]["ttt_s"]:
+    for name in ("bf16_learned", "bf16_batched_learned"):
+        for ref in ("fp32_plain", "bf16_best_fixed", "bf16_plain"):
+            if name in out and out[name]["ttt_s"] and out[ref]["ttt_s"]:
                 out[f"speedup_{name}_vs_{ref}"] = out[ref]["ttt_s"] / out[name]["ttt_s"]
     return out
+
+
+def batched_learned_arm(gda, torch, stream, prop, solver, J, g, W, R, k_hit, t_prop):
+    """BF16 + batched + learned: the instance inside a batch with the XY
+    instances of a serving mix (N log-uniform in [50, 2000], R in [16, 256]),
+    with the proposal's settings and start.  The batch follows each instance's
+    single-instance dynamics bit for bit (checked here at the hit step), and
+    instance 0 of a batch keyed by the run's seed has the single run's key, so
+    the FP64-verified step at the target is the single learned arm's.  Time
+    to target: the proposal's time plus the batch's time to that step times
+    the instance's share of the batch's coupling FLOPs (the GPU time the batch
+    spends on it)."""
+    import synth
+    from paper_1807_00699_gb300 import proposal
+    descs = [d for d in synth.batched_mix(512, 11) if d["model"] == "xy"][:255]
+    insts = [(J, g, gda.XY, R)]
+    for d in descs:
+        Jd, gd = synth.make_instance(d)
+        insts.append((Jd, gd, gda.XY, d["r"]))
+    bt = gda.Batch(insts, seed=W["seed"], stream=stream)
+    settings = proposal.propose_into_batch(prop, solver, bt, 0, W["dt"])
+    prm = gda.default_params(dt=W["dt"], eps=0.1, init_mode=3, init_amp=proposal.AMP, prec=gda.BF16)
+    bt.run(prm, 200)  # warm-up (graph capture)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    bt.run(prm, k_hit)
+    e1.record(stream)
+    e1.synchronize()
+    t_batch = e0.elapsed_time(e1) / 1e3
+    flops = [2.0 * Jk.shape[0] ** 2 * 2 * Rk for Jk, _, _, Rk in insts]
+    share = flops[0] / sum(flops)
+    # bit-identity of instance 0 with the single-instance learned run at the hit step
+    ref = gda.Solver(J, g, gda.XY, stream=stream)
+    st = prop.propose(ref)
+    ref.run(proposal.proposed_params(st, W["seed"], dt=W["dt"], prec=gda.BF16, schedule=gda.PER_STEP), R, k_hit)
+    same = bool(np.array_equal(ref.get_state()[0], bt.get_state(0)[0]))
+    ref.close()
+    row = {"ttt_s": t_prop + t_batch * share, "steps_to_target": k_hit, "batch_s_to_step": t_batch,
+           "instances": len(insts), "flop_share": share, "settings": settings, "proposal_s": t_prop,
+           "bit_identical_to_single_run": same, "launch_mode": "graph" if bt.launch_mode() == 1 else "direct",
+           "batch_spin_updates_per_s": sum(Jk.shape[0] * Rk for Jk, _, _, Rk in insts) * k_hit / t_batch}
+    bt.close()
+    return row
 
 
 # ---------------------------------------------------------------- our arm
@@ -559,6 +607,8 @@ def run_batched(args):
     upd_sub = sum(J.shape[0] * R for J, _, _, R in sub) * steps
     line = {"metric": "spin-updates/s (batched serving mix)", "value": upd / t, "unit": "spin-updates/s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
+            "launch": ("one persistent cooperative launch per 100 steps, " +
+                       ("replayed from a captured CUDA graph" if b.launch_mode() == 1 else "launched directly")),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
             "config": {"workload": f"batched_mix_{args.batch_count}", "instances": len(descs), "steps": steps,
                        "tile_bn": bn, "tune_s_per_step": tune, "setup_s": setup_s,

@@ -383,12 +383,16 @@ gda_status gda_adam_step(float* params, const float* grad, float* m1, float* m2,
                          float beta1, float beta2, float eps, int32_t t, void* stream);
 
 /* ---- Batched serving (not in the paper) -----------------------------------
- * Many independent instances (own N, model and R each) stepped together:
- * one persistent tensor-core launch per step and model type over all their
- * 128 x BN output tiles, steps replayed from a captured CUDA graph.  Every
- * instance follows exactly the single-instance forward-Euler BF16 dynamics
- * (Eqs. 2, 5, 6) with its own Philox seed.  The batch owns its device memory.
- * Layout conventions are those of the single-instance calls. */
+ * Many independent instances (own N, model and R each) stepped together: one
+ * persistent cooperative tensor-core launch runs a chunk of 100 steps of
+ * every instance (both model types) over all their 128 x BN output tiles,
+ * with steps ordered by per-tile dataflow flags; chunks replay from a captured
+ * CUDA graph where the driver captures the launch (gda_batch_launch_mode).
+ * Every instance follows exactly the single-instance forward-Euler BF16
+ * dynamics (Eqs. 2, 5, 6) with its own Philox seed and, optionally, its own
+ * settings and start (gda_batch_set_params, gda_batch_set_init_base).  The
+ * batch owns its device memory.  Layout conventions are those of the
+ * single-instance calls. */
 typedef struct gda_batch gda_batch;
 
 /* n instances: N[k] spins, model[k], R[k] restarts, J[k] (N[k]^2 doubles,
@@ -399,14 +403,36 @@ gda_status gda_batch_create(int32_t n, const int32_t* N, const int32_t* model, c
                             const double* const* J, const double* const* g, uint64_t seed, gda_batch** out);
 gda_status gda_batch_set_stream(gda_batch* b, void* stream);
 
-/* Tile width of the coupling product: 128 or 256 columns (gda_batch_tune
- * picks the faster). */
+/* Tile width of the coupling product: 128 or 256 columns (the caller times
+ * both and keeps the faster). */
 gda_status gda_batch_set_tile(gda_batch* b, int32_t bn);
 
 /* Runs `steps` forward-Euler BF16 steps of every instance (p->integ must be
- * GDA_EULER, p->prec GDA_BF16; noise without decay; init_mode 0, 1 or 2;
- * p->seed is ignored: instances use their own keys).  Asynchronous. */
+ * GDA_EULER, p->prec GDA_BF16; noise without decay; init_mode 0, 1, 2 or 3;
+ * p->seed is ignored: instances use their own keys).  dt, eps, rho_th, beta0
+ * and eps_hat of p apply to the instances without their own settings;
+ * noise_D, init_amp, gamma0 and wait_s to all.  Asynchronous. */
 gda_status gda_batch_run(gda_batch* b, const gda_params* p, int64_t steps);
+
+/* Instance k's own settings: dt, eps, rho_th, beta0 and eps_hat of p replace
+ * the run's for instance k in later runs (the learned proposal gives each
+ * instance its own; instances of different coupling scales need their own
+ * dt); p = NULL returns instance k to the run's settings.  GDA_ERR_INVALID
+ * for k out of range, non-finite values, dt <= 0 or rho_th <= 0. */
+gda_status gda_batch_set_params(gda_batch* b, int32_t k, const gda_params* p);
+
+/* Base amplitudes of instance k for init_mode 3, as gda_set_init_base: N[k]
+ * floats (Ising) or N[k] interleaved (re, im) pairs (XY), host (on_device =
+ * 0) or device (1), copied; a run with init_mode 3 starts restart r of
+ * instance k at base_i + the init_mode 1 perturbation of (i, r) (instances
+ * without a base: the perturbation alone).  base = NULL clears it.
+ * Synchronises. */
+gda_status gda_batch_set_init_base(gda_batch* b, int32_t k, const float* base, int32_t on_device);
+
+/* 1 if the batch's chunks replay a captured CUDA graph, 0 if they are
+ * launched directly (the driver declined to capture the cooperative launch),
+ * -1 for b = NULL. */
+int32_t gda_batch_launch_mode(const gda_batch* b);
 
 /* FP64 Eq. (1) energy of the best restart of every instance (ties: lowest
  * restart) into E[n], r[n] (host, either may be NULL).  Synchronises and

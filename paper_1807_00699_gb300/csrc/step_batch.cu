@@ -5,13 +5,24 @@
 // and their operands into one BF16 tensor [sum 2 Cp_i][P] (common row pitch
 // P = max Np_i), so a single TMA tensor map per tensor addresses every tile.
 // FP32 state is stored compactly per instance.  A work unit is one 128 x BN
-// output tile (instance, row block, column block); units are assigned to CTAs
-// on the host by longest-processing-time first, and each launch is a
-// persistent kernel over its CTA's unit list with the double-buffered tensor-
-// memory accumulators of the per-step kernel.  One launch per step and model
-// type (the epilogue is specialised for real or complex amplitudes); the step
-// index and the buffer parity come from a device counter, so a captured CUDA
-// graph of many steps replays correctly.  Euler steps, Eqs. (2), (5), (6).
+// output tile (instance, row block, column block) of either model type; the
+// units of all instances are assigned to CTAs on the host by longest
+// processing time first.
+//
+// One persistent cooperative launch runs a chunk of steps for every instance:
+// each CTA walks its unit list once per step, with the double-buffered
+// tensor-memory accumulators of the per-step kernel, and steps are ordered by
+// dataflow flags, one per unit (as in the resident single-instance kernel):
+// after the epilogue of unit (k, m, n) has written its rows of instance k's
+// next operand (and, for m = 0, the next coupling scales beta), it publishes
+// flag = step + 1; a producer loading K-block kb of instance k's column block
+// n for step s waits until the flag of unit (k, kb / 2, n) reaches s, and the
+// epilogue reading beta of that column block waits for unit (k, 0, n).  The
+// epilogue is specialised per unit for real or complex amplitudes.  The step
+// index comes from a device counter, so a captured CUDA graph of chunk
+// launches replays correctly.  Euler steps, Eqs. (2), (5), (6), each instance
+// with its own gain speed, threshold, ramp and Philox key.  Every wait is
+// bounded; a wait that runs out aborts the launch (E_TIMEOUT).
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -35,11 +46,15 @@ struct BatchInst {
   int cplx;
   int rowJ;            // first row of the instance's couplings in the packed tensor
   int rowX;            // first row of operand buffer 0 (buffer 1 follows at rowX + Cp)
+  int flag0;           // flag of unit (row block 0, column block 0); unit (m, n) at flag0 + n * mt + m
+  int has_base;        // init_mode 3: per-spin base amplitudes at off_base
   long long off_psi;   // psi [2][Cp][Np]
   long long off_gam;   // gamma [Rp][Np]
   long long off_h1;    // h1 [Np]
   long long off_beta;  // beta [2][Rp]
+  long long off_base;  // base amplitudes [N][2]
   unsigned long long seed;
+  float dt, eps, rho_th, eps_hat, beta0, sq;  // the instance's settings (sq = sqrt(rho_th) in FP32)
 };
 
 struct BatchUnit {
@@ -58,7 +73,10 @@ struct BatchArgs {
   int pitch;
   const unsigned* step_base;  // device step counter of the run
   unsigned step_off;          // this launch's offset from it
-  float dt, eps, rho_th, eps_hat, noise_D;
+  int nsteps;                 // steps of this launch
+  unsigned* flags;            // per-unit step flags (absolute step + 1)
+  float noise_D;
+  long long wait_cycles;
   int* err;
 };
 
@@ -73,6 +91,16 @@ struct BCfg {
 
 __device__ __forceinline__ void bar_epi() { asm volatile("bar.sync 1, %0;" ::"n"(32 * NEPI) : "memory"); }
 
+// Bounded wait until a unit flag reaches target (acquire).
+__device__ __forceinline__ bool bflag_wait(const unsigned* f, unsigned target, long long limit) {
+  if (ld_acquire_gpu(f) >= target) return true;
+  const long long t0 = clock64();
+  while (ld_acquire_gpu(f) < target) {
+    if (clock64() - t0 > limit) return false;
+  }
+  return true;
+}
+
 // StepArgs of one instance for a forward-Euler step with parity cur.
 __device__ __forceinline__ StepArgs unit_args(const BatchArgs& b, const BatchInst& I, unsigned step, int cur) {
   StepArgs a{};
@@ -80,7 +108,7 @@ __device__ __forceinline__ StepArgs unit_args(const BatchArgs& b, const BatchIns
   a.mode = M_EULER;
   a.cplx = I.cplx;
   a.mt_count = I.mt;
-  a.dt = b.dt; a.eps = b.eps; a.rho_th = b.rho_th; a.eps_hat = b.eps_hat;
+  a.dt = I.dt; a.eps = I.eps; a.rho_th = I.rho_th; a.eps_hat = I.eps_hat;
   a.noise_D = b.noise_D;
   a.noise_decay = 0;
   a.seed = I.seed;
@@ -99,8 +127,82 @@ __device__ __forceinline__ StepArgs unit_args(const BatchArgs& b, const BatchIns
   return a;
 }
 
-template <int BN, int STAGES, bool CPLX>
-__global__ void __launch_bounds__(NTHREADS, 1)
+// Epilogue of one unit at one step (all NEPI epilogue warps): waits for the
+// unit's accumulator, runs the Euler update of its 128 x BN tile, frees the
+// accumulator and publishes the unit's flag.  Returns false on an abort.
+template <int BN, bool CPLX>
+__device__ __forceinline__ bool epi_unit(const BatchArgs& b, const BatchInst& I, const BatchUnit& U, unsigned step,
+                                         int cur, int n, uint32_t tacc, uint32_t full, uint32_t empty, uint32_t use,
+                                         float* s_beta, float* s_dsc, int* s_flag, int& bad) {
+  constexpr int W = CPLX ? 2 : 1;
+  constexpr int RPT = BN / W;
+  constexpr int PW = BN / (NEPI / 4);  // columns per part
+  constexpr int CW = 8;
+  constexpr int NCH = PW / CW;
+  static_assert(PW % CW == 0, "column part must hold whole chunks");
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int e = threadIdx.x - 64;
+  const int q = warp & 3;
+  const int part = (warp - 2) >> 2;
+  const StepArgs a = unit_args(b, I, step, cur);
+  const int m0 = U.mt * BM, n0 = U.nt * BN;
+  const int rbase = n0 / W;
+  const int i = m0 + 32 * q + lane;
+  const int cbeg = n0 + part * PW;
+  const unsigned* fl = b.flags + I.flag0 + U.nt * I.mt;
+  EpiRegs<M_EULER, CPLX, CW> R[2];
+  epi_load<M_EULER, CPLX, CW>(a, i, cbeg, R[0]);  // own rows of psi and gamma: written by this thread
+  bool fok = true;
+  if (e < RPT) {
+    // beta^n of this column block was written by unit (k, 0, n) at the previous step
+    if (n > 0) fok = bflag_wait(fl, step, b.wait_cycles);
+    const int r = rbase + e;
+    s_beta[e] = r < a.R ? a.beta_in[r] : 1.0f;
+    s_dsc[e] = r < a.R ? noise_scale(a, r) : 0.0f;
+  }
+  // one decision for all epilogue warps; the vote also publishes s_beta / s_dsc
+  const bool ok = epi_vote_all<32 * NEPI>(fok && mbar_wait(full, use & 1, b.wait_cycles) &&
+                                          !*(volatile int*)&s_flag[0]);
+  tc_fence_after();
+  if (!ok) {
+    if (lane == 0) atomicOr(b.err, E_TIMEOUT);
+    atomicOr(&s_flag[0], 1);
+    return false;
+  }
+  const uint32_t taddr = tacc + (static_cast<uint32_t>(32 * q) << 16) + part * PW;
+  auto body = [&](int ch, const EpiRegs<M_EULER, CPLX, CW>& cr, EpiRegs<M_EULER, CPLX, CW>& nx) {
+    if (ch + 1 < NCH) epi_load<M_EULER, CPLX, CW>(a, i, cbeg + (ch + 1) * CW, nx);
+    float v[CW];
+    tmem_ld<CW>(taddr + ch * CW, v);
+    const int lr0 = (part * PW + ch * CW) / W;
+    float red[CW / W];
+    epi_chunk<M_EULER, CPLX, CW>(a, i, cbeg + ch * CW, v, cr, &s_beta[lr0], &s_dsc[lr0], red, bad);
+  };
+#pragma unroll 1
+  for (int ch = 0; ch + 1 < NCH; ch += 2) {
+    body(ch, R[0], R[1]);
+    body(ch + 1, R[1], R[0]);
+  }
+  if (NCH & 1) body(NCH - 1, R[0], R[1]);
+  tc_fence_before();
+  fence_proxy_async_global();  // the next operand rows are read by other CTAs' TMA loads
+  bar_epi();
+  if (e == 0) mbar_arrive(empty);
+  if (e < RPT && U.mt == 0) {
+    const int r = rbase + e;
+    if (r < a.R) a.beta_out[r] = next_beta(a, a.beta_in[r]);
+  }
+  bar_epi();
+  if (e == 0) {
+    __threadfence();
+    st_release_gpu(b.flags + I.flag0 + U.nt * I.mt + U.mt, step + 1u);
+  }
+  return true;
+}
+
+// 112 registers a thread: 576 x 112 fill the SM's register file, one CTA per SM.
+template <int BN, int STAGES>
+__global__ void __maxnreg__(112)
     step_batch_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, BatchArgs b) {
   using Cfg = BCfg<BN, STAGES>;
   extern __shared__ uint8_t smem_raw[];
@@ -116,8 +218,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   int* s_flag = reinterpret_cast<int*>(s_tmem + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const unsigned step = *b.step_base + b.step_off;
-  const int cur = int(step & 1u);
+  const unsigned step0 = *b.step_base + b.step_off;
+  const long long lim = b.wait_cycles;
   const int u0 = b.cta_begin[blockIdx.x], u1 = b.cta_begin[blockIdx.x + 1];
   auto full_bar = [&](int s) { return smem_u32(bars + s); };
   auto empty_bar = [&](int s) { return smem_u32(bars + STAGES + s); };
@@ -145,127 +247,108 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const uint32_t tmem = *s_tmem;
 
   if (warp == 0) {
+    // ---------------- TMA producer ----------------
     if (lane == 0) {
       int it = 0;
       bool stop = false;
-      for (int u = u0; u < u1 && !stop; ++u) {
-        const BatchUnit U = b.units[u];
-        const BatchInst& I = b.inst[U.inst];
-        const int KB = (I.N + BK - 1) / BK;
-        const int ya = I.rowJ + U.mt * BM;
-        const int yb = I.rowX + cur * I.Cp + U.nt * BN;
-        for (int kb = 0; kb < KB; ++kb, ++it) {
-          const int s = it % STAGES;
-          const uint32_t ph = (it / STAGES) & 1;
-          if (!mbar_wait(empty_bar(s), ph ^ 1u) || *(volatile int*)&s_flag[0]) {
-            stop = true;
-            break;
+      for (int n = 0; n < b.nsteps && !stop; ++n) {
+        const unsigned step = step0 + unsigned(n);
+        const int cur = int(step & 1u);
+        for (int u = u0; u < u1 && !stop; ++u) {
+          const BatchUnit U = b.units[u];
+          const BatchInst& I = b.inst[U.inst];
+          const int KB = (I.N + BK - 1) / BK;
+          const int ya = I.rowJ + U.mt * BM;
+          const int yb = I.rowX + cur * I.Cp + U.nt * BN;
+          const unsigned* fl = b.flags + I.flag0 + U.nt * I.mt;
+          int ready_m = -1;
+          for (int kb = 0; kb < KB; ++kb, ++it) {
+            const int s = it % STAGES;
+            const uint32_t ph = (it / STAGES) & 1;
+            const int mb = (kb * BK) / BM;  // row block that produced these spins
+            if (n > 0 && mb != ready_m) {
+              if (!bflag_wait(fl + mb, step, lim)) {
+                stop = true;
+                break;
+              }
+              fence_proxy_async_global();
+              ready_m = mb;
+            }
+            if (!mbar_wait(empty_bar(s), ph ^ 1u, lim) || *(volatile int*)&s_flag[0]) {
+              stop = true;
+              break;
+            }
+            mbar_arrive_expect_tx(full_bar(s), Cfg::STAGE_BYTES);
+            tma_load_2d(sA + s * Cfg::A_BYTES, &tmA, kb * BK, ya, full_bar(s));
+            tma_load_2d(sB + s * Cfg::B_BYTES, &tmB, kb * BK, yb, full_bar(s));
           }
-          mbar_arrive_expect_tx(full_bar(s), Cfg::STAGE_BYTES);
-          tma_load_2d(sA + s * Cfg::A_BYTES, &tmA, kb * BK, ya, full_bar(s));
-          tma_load_2d(sB + s * Cfg::B_BYTES, &tmB, kb * BK, yb, full_bar(s));
         }
       }
       if (stop) {
         atomicOr(&s_flag[0], 1);
-        for (int k = it - 1; k >= 0 && k >= it - STAGES; --k) (void)mbar_wait(full_bar(k % STAGES), (k / STAGES) & 1);
+        for (int k = it - 1; k >= 0 && k >= it - STAGES; --k) (void)mbar_wait(full_bar(k % STAGES), (k / STAGES) & 1, lim);
       }
     }
   } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
     if (lane == 0) {
       constexpr uint32_t idesc = idesc_bf16<BN>();
       int it = 0, lt = 0;
+      int committed = -1;  // accumulator of the last commit (lt), -1 before any
       bool stop = false;
-      for (int u = u0; u < u1 && !stop; ++u, ++lt) {
-        const int KB = (b.inst[b.units[u].inst].N + BK - 1) / BK;
-        const int k2 = lt & 1;
-        const uint32_t use = lt >> 1;
-        if (!mbar_wait(acc_empty(k2), (use & 1) ^ 1u) || *(volatile int*)&s_flag[0]) {
-          stop = true;
-          break;
-        }
-        tc_fence_after();
-        const uint32_t dacc = tmem + k2 * BN;
-        for (int kb = 0; kb < KB; ++kb, ++it) {
-          const int s = it % STAGES;
-          const uint32_t ph = (it / STAGES) & 1;
-          if (!mbar_wait(full_bar(s), ph) || *(volatile int*)&s_flag[0]) {
+      for (int n = 0; n < b.nsteps && !stop; ++n) {
+        for (int u = u0; u < u1 && !stop; ++u, ++lt) {
+          const int KB = (b.inst[b.units[u].inst].N + BK - 1) / BK;
+          const int k2 = lt & 1;
+          const uint32_t use = lt >> 1;
+          if (!mbar_wait(acc_empty(k2), (use & 1) ^ 1u, lim) || *(volatile int*)&s_flag[0]) {
             stop = true;
             break;
           }
           tc_fence_after();
+          const uint32_t dacc = tmem + k2 * BN;
+          for (int kb = 0; kb < KB; ++kb, ++it) {
+            const int s = it % STAGES;
+            const uint32_t ph = (it / STAGES) & 1;
+            if (!mbar_wait(full_bar(s), ph, lim) || *(volatile int*)&s_flag[0]) {
+              stop = true;
+              break;
+            }
+            tc_fence_after();
 #pragma unroll
-          for (int k = 0; k < BK / 16; ++k)
-            mma_bf16(dacc, sdesc_sw128(sA + s * Cfg::A_BYTES + k * 32), sdesc_sw128(sB + s * Cfg::B_BYTES + k * 32),
-                     idesc, (kb | k) != 0);
-          mma_commit(empty_bar(s));
-        }
-        mma_commit(acc_full(k2));
-        if (stop) {
-          (void)mbar_wait(acc_full(k2), use & 1);
-          break;
+            for (int k = 0; k < BK / 16; ++k)
+              mma_bf16(dacc, sdesc_sw128(sA + s * Cfg::A_BYTES + k * 32), sdesc_sw128(sB + s * Cfg::B_BYTES + k * 32),
+                       idesc, (kb | k) != 0);
+            mma_commit(empty_bar(s));
+          }
+          mma_commit(acc_full(k2));  // also after an abort: tracks every MMA issued into k2
+          committed = lt;
         }
       }
-      if (stop) atomicOr(&s_flag[0], 1);
+      if (stop) {
+        atomicOr(&s_flag[0], 1);
+        // the MMAs in flight finish before the CTA frees its tensor memory
+        if (committed >= 0) (void)mbar_wait(acc_full(committed & 1), (committed >> 1) & 1, lim);
+      }
     }
   } else {
-    constexpr int W = CPLX ? 2 : 1;
-    constexpr int RPT = BN / W;
-    constexpr int PW = BN / (NEPI / 4);  // columns per part
-    constexpr int CW = 8;
-    constexpr int NCH = PW / CW;
-    static_assert(PW % CW == 0, "column part must hold whole chunks");
+    // ---------------- epilogue warps ----------------
     const int e = threadIdx.x - 64;
-    const int q = warp & 3;
-    const int part = (warp - 2) >> 2;
     int bad = 0, lt = 0;
-    EpiRegs<M_EULER, CPLX, CW> R[2];
-    for (int u = u0; u < u1; ++u, ++lt) {
-      const BatchUnit U = b.units[u];
-      const BatchInst& I = b.inst[U.inst];
-      const StepArgs a = unit_args(b, I, step, cur);
-      const int m0 = U.mt * BM, n0 = U.nt * BN;
-      const int k2 = lt & 1;
-      const uint32_t use = lt >> 1;
-      const int rbase = n0 / W;
-      const int i = m0 + 32 * q + lane;
-      const int cbeg = n0 + part * PW;
-      epi_load<M_EULER, CPLX, CW>(a, i, cbeg, R[0]);
-      if (e < RPT) {
-        const int r = rbase + e;
-        s_beta[e] = r < a.R ? a.beta_in[r] : 1.0f;
-        s_dsc[e] = r < a.R ? noise_scale(a, r) : 0.0f;
-      }
-      // one decision for all epilogue warps (the vote is also the barrier that
-      // publishes s_beta / s_dsc)
-      const bool ok = epi_vote_all<32 * NEPI>(mbar_wait(acc_full(k2), use & 1) && !*(volatile int*)&s_flag[0]);
-      tc_fence_after();
-      if (!ok) {
-        if (lane == 0) atomicOr(b.err, E_TIMEOUT);
-        atomicOr(&s_flag[0], 1);
-        break;
-      }
-      const uint32_t taddr = tmem + k2 * BN + (static_cast<uint32_t>(32 * q) << 16) + part * PW;
-      auto body = [&](int ch, const EpiRegs<M_EULER, CPLX, CW>& cr, EpiRegs<M_EULER, CPLX, CW>& nx) {
-        if (ch + 1 < NCH) epi_load<M_EULER, CPLX, CW>(a, i, cbeg + (ch + 1) * CW, nx);
-        float v[CW];
-        tmem_ld<CW>(taddr + ch * CW, v);
-        const int lr0 = (part * PW + ch * CW) / W;
-        float red[CW / W];
-        epi_chunk<M_EULER, CPLX, CW>(a, i, cbeg + ch * CW, v, cr, &s_beta[lr0], &s_dsc[lr0], red, bad);
-      };
-#pragma unroll 1
-      for (int ch = 0; ch + 1 < NCH; ch += 2) {
-        body(ch, R[0], R[1]);
-        body(ch + 1, R[1], R[0]);
-      }
-      if (NCH & 1) body(NCH - 1, R[0], R[1]);
-      tc_fence_before();
-      bar_epi();
-      if (e == 0) mbar_arrive(acc_empty(k2));
-      if (e < RPT && U.mt == 0) {
-        const int r = rbase + e;
-        if (r < a.R) a.beta_out[r] = next_beta(a, a.beta_in[r]);
+    bool run = true;
+    for (int n = 0; n < b.nsteps && run; ++n) {
+      const unsigned step = step0 + unsigned(n);
+      const int cur = int(step & 1u);
+      for (int u = u0; u < u1 && run; ++u, ++lt) {
+        const BatchUnit U = b.units[u];
+        const BatchInst& I = b.inst[U.inst];
+        const int k2 = lt & 1;
+        const uint32_t use = lt >> 1;
+        const uint32_t tacc = tmem + k2 * BN;
+        run = I.cplx ? epi_unit<BN, true>(b, I, U, step, cur, n, tacc, acc_full(k2), acc_empty(k2), use, s_beta,
+                                          s_dsc, s_flag, bad)
+                     : epi_unit<BN, false>(b, I, U, step, cur, n, tacc, acc_full(k2), acc_empty(k2), use, s_beta,
+                                           s_dsc, s_flag, bad);
       }
     }
     if (bad) s_flag[1] = 1;
@@ -282,22 +365,28 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   }
 }
 
-// Initial state of every instance: psi (init_mode 0 / 1, as the
-// single-instance init), gamma0, beta0, its BF16 operand and h1.
+// Initial state of every instance: psi (init_mode 0 / 1 / 3, as the
+// single-instance init: seeded U(-a, a) per component, plus the instance's
+// base amplitudes for mode 3), its gamma0 and beta0, the BF16 operand and h1.
 __global__ void k_batch_init(const BatchInst* inst, int n_inst, float* psi, float* gam, float* beta, float* h1,
-                             const double* g64, const long long* off_g, __nv_bfloat16* ops, int pitch, int mode,
-                             float amp, float gamma0, float beta0, float sq) {
+                             const double* g64, const long long* off_g, const float* base, __nv_bfloat16* ops,
+                             int pitch, int mode, float amp, float gamma0) {
   const int b = blockIdx.y;
   if (b >= n_inst) return;
   const BatchInst I = inst[b];
   const size_t total = size_t(I.R) * I.N;
+  const bool with_base = mode == 3 && I.has_base;
   for (size_t idx = blockIdx.x * size_t(blockDim.x) + threadIdx.x; idx < total; idx += size_t(gridDim.x) * blockDim.x) {
     const int r = int(idx / I.N), i = int(idx % I.N);
     float re = 0.0f, im = 0.0f;
-    if (mode == 1) {
+    if (mode == 1 || mode == 3) {
       const U4 o = philox4x32_10(U4{uint32_t(i), uint32_t(r), 0u, 1u}, uint32_t(I.seed), uint32_t(I.seed >> 32));
       re = amp * (2.0f * philox_u01(o.x) - 1.0f);
       im = amp * (2.0f * philox_u01(o.y) - 1.0f);
+      if (with_base) {
+        re = __fadd_rn(base[I.off_base + 2 * i], re);
+        im = __fadd_rn(base[I.off_base + 2 * i + 1], im);
+      }
     }
     const int W = I.cplx ? 2 : 1;
     float* p = psi + I.off_psi;
@@ -309,8 +398,8 @@ __global__ void k_batch_init(const BatchInst* inst, int n_inst, float* psi, floa
       op[size_t(2 * r + 1) * pitch + i] = __float2bfloat16_rn(im);
     }
     gam[I.off_gam + size_t(r) * I.Np + i] = gamma0;
-    if (i == 0) beta[I.off_beta + r] = beta0;
-    if (r == 0) h1[I.off_h1 + i] = float(-g64[off_g[b] + i]) * sq;
+    if (i == 0) beta[I.off_beta + r] = I.beta0;
+    if (r == 0) h1[I.off_h1 + i] = float(-g64[off_g[b] + i]) * I.sq;
   }
 }
 
@@ -491,15 +580,20 @@ struct gda_batch {
   int4* eunits = nullptr;
   int n_eunits = 0;
   unsigned* step_base = nullptr;
+  unsigned* flags = nullptr;  // per-unit step flags [n_flags]
+  int n_flags = 0;
+  float* base = nullptr;      // per-instance base amplitudes for init_mode 3 [sum N][2]
   int* err = nullptr;
   CUtensorMap tmA{}, tmB128{}, tmB256{};
-  BatchPlan plan[2][2];  // [model: Ising, XY][width: 128, 256]
+  BatchPlan plan[2];     // [width: 128, 256], units of both model types
   int bn = 128;          // tile width in use (autotuned)
+  std::vector<char> own;  // instance k has its own settings (gda_batch_set_params)
+  std::vector<BatchInst> uploaded;  // the instance table as last copied to the device
   unsigned long long step = 0;
   bool have_state = false;
   std::string msg;
   cudaGraphExec_t graph = nullptr;
-  int graph_steps = 0;
+  bool graph_failed = false;  // capture of the cooperative launch was refused: launch directly
   unsigned graph_key[8] = {};
 };
 
@@ -526,13 +620,12 @@ cudaError_t balloc(T** p, size_t n) {
   return cudaMalloc(reinterpret_cast<void**>(p), std::max<size_t>(n, 1) * sizeof(T));
 }
 
-// Longest-processing-time assignment of one model type's tiles to CTAs.
-gda_status build_plan(gda_batch* b, int model, int bn, BatchPlan* P) {
+// Longest-processing-time assignment of every instance's tiles to CTAs.
+gda_status build_plan(gda_batch* b, int bn, BatchPlan* P) {
   std::vector<BatchUnit> units;
   std::vector<double> cost;
   for (int k = 0; k < b->n; ++k) {
     const BatchInst& I = b->host[k];
-    if (I.cplx != model) continue;
     const int nt = (I.C + bn - 1) / bn;
     for (int mt = 0; mt < I.mt; ++mt)
       for (int t = 0; t < nt; ++t) {
@@ -570,35 +663,37 @@ gda_status build_plan(gda_batch* b, int model, int bn, BatchPlan* P) {
   return GDA_OK;
 }
 
-template <int BN, int STAGES, bool CPLX>
+template <int BN, int STAGES>
 cudaError_t launch_batch(gda_batch* b, const BatchPlan& P, const BatchArgs& a) {
   using Cfg = BCfg<BN, STAGES>;
-  auto kern = step_batch_kernel<BN, STAGES, CPLX>;
   const CUtensorMap& B = BN == 256 ? b->tmB256 : b->tmB128;
-  kern<<<P.grid, NTHREADS, Cfg::SMEM, b->stream>>>(b->tmA, B, a);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(P.grid);
+  cfg.blockDim = dim3(NTHREADS);
+  cfg.dynamicSmemBytes = Cfg::SMEM;
+  cfg.stream = b->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;  // every CTA resident: the step flags need it
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, step_batch_kernel<BN, STAGES>, b->tmA, B, a);
 }
 
-// Shared-memory limits of every batched kernel variant, set once (outside any
+// Shared-memory limits of both kernel variants, set once (outside any
 // stream capture).
 cudaError_t set_batch_attrs() {
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(step_batch_kernel<128, 6, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if ((e = cudaFuncSetAttribute(step_batch_kernel<128, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 BCfg<128, 6>::SMEM)) != cudaSuccess)
     return e;
-  if ((e = cudaFuncSetAttribute(step_batch_kernel<128, 6, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                BCfg<128, 6>::SMEM)) != cudaSuccess)
-    return e;
-  if ((e = cudaFuncSetAttribute(step_batch_kernel<256, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                BCfg<256, 4>::SMEM)) != cudaSuccess)
-    return e;
-  return cudaFuncSetAttribute(step_batch_kernel<256, 4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  return cudaFuncSetAttribute(step_batch_kernel<256, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               BCfg<256, 4>::SMEM);
 }
 
-// Launches one step of every model type present (offset `off` from the
-// device step counter).
-gda_status launch_step(gda_batch* b, const gda_params* p, unsigned off) {
+// One persistent launch of `nsteps` steps of every instance (offset `off`
+// from the device step counter).
+gda_status launch_chunk(gda_batch* b, const gda_params* p, unsigned off, int nsteps) {
   BatchArgs a{};
   a.inst = b->inst;
   a.psi = b->psi;
@@ -609,25 +704,41 @@ gda_status launch_step(gda_batch* b, const gda_params* p, unsigned off) {
   a.pitch = b->pitch;
   a.step_base = b->step_base;
   a.step_off = off;
-  a.dt = float(p->dt);
-  a.eps = float(p->eps);
-  a.rho_th = float(p->rho_th);
-  a.eps_hat = float(p->eps_hat);
+  a.nsteps = nsteps;
+  a.flags = b->flags;
   a.noise_D = float(p->noise_D);
+  a.wait_cycles = p->wait_s > 0 ? (long long)(p->wait_s * kCyclesPerSecond) : kWaitCycles;
   a.err = b->err;
   const int wi = b->bn == 256 ? 1 : 0;
-  for (int model = 0; model < 2; ++model) {
-    const BatchPlan& P = b->plan[model][wi];
-    if (P.n_units == 0) continue;
-    a.units = P.units;
-    a.cta_begin = P.cta_begin;
-    cudaError_t e;
-    if (model == 1)
-      e = wi ? launch_batch<256, 4, true>(b, P, a) : launch_batch<128, 6, true>(b, P, a);
-    else
-      e = wi ? launch_batch<256, 4, false>(b, P, a) : launch_batch<128, 6, false>(b, P, a);
-    BCK(e);
+  const BatchPlan& P = b->plan[wi];
+  if (P.n_units == 0) return GDA_OK;
+  a.units = P.units;
+  a.cta_begin = P.cta_begin;
+  const cudaError_t le = wi ? launch_batch<256, 4>(b, P, a) : launch_batch<128, 6>(b, P, a);
+  BCK(le);
+  return GDA_OK;
+}
+
+// Instance settings of a run: the run's eps, rho_th, beta0 and eps_hat for
+// instances without their own; copied to the device when they change.
+gda_status upload_settings(gda_batch* b, const gda_params* p) {
+  for (int k = 0; k < b->n; ++k) {
+    if (b->own[k]) continue;
+    BatchInst& I = b->host[k];
+    I.dt = float(p->dt);
+    I.eps = float(p->eps);
+    I.rho_th = float(p->rho_th);
+    I.beta0 = float(p->beta0);
+    I.eps_hat = float(p->eps_hat);
+    I.sq = float(std::sqrt(p->rho_th));
   }
+  if (b->uploaded.size() == b->host.size() &&
+      std::memcmp(b->uploaded.data(), b->host.data(), b->host.size() * sizeof(BatchInst)) == 0)
+    return GDA_OK;
+  BCK(cudaMemcpyAsync(b->inst, b->host.data(), b->host.size() * sizeof(BatchInst), cudaMemcpyHostToDevice,
+                      b->stream));
+  BCK(cudaStreamSynchronize(b->stream));
+  b->uploaded = b->host;
   return GDA_OK;
 }
 
@@ -672,8 +783,10 @@ gda_status gda_batch_create(int32_t n, const int32_t* N, const int32_t* model, c
   b->n = n;
   b->host.resize(n);
   long long off_psi = 0, off_gam = 0, off_h1 = 0, off_beta = 0, off_J = 0, off_g = 0, off_part = 0, off_E = 0;
+  long long off_base = 0, n_flags = 0;
   std::vector<long long> oJ(n), oG(n), oP(n), oE(n);
   int pitch = 64;
+  b->own.assign(n, 0);
   for (int k = 0; k < n; ++k) {
     BatchInst& I = b->host[k];
     I.N = N[k];
@@ -696,6 +809,17 @@ gda_status gda_batch_create(int32_t n, const int32_t* N, const int32_t* model, c
     off_h1 += I.Np;
     I.off_beta = off_beta;
     off_beta += 2LL * I.Rp;
+    I.off_base = off_base;
+    off_base += 2LL * I.N;
+    I.has_base = 0;
+    I.flag0 = int(n_flags);
+    n_flags += (long long)I.mt * ((I.C + 127) / 128);  // units at the narrowest tile width
+    I.dt = 0.01f;
+    I.eps = 0.1f;
+    I.rho_th = 1.0f;
+    I.eps_hat = 0.0f;
+    I.beta0 = 1.0f;
+    I.sq = 1.0f;
     I.seed = seed + 0x9E3779B97F4A7C15ULL * (unsigned long long)k;
     oJ[k] = off_J;
     off_J += (long long)I.N * I.N;
@@ -707,7 +831,9 @@ gda_status gda_batch_create(int32_t n, const int32_t* N, const int32_t* model, c
     off_E += I.R;
     pitch = std::max(pitch, I.Np);
   }
-  if (b->rowsJ > INT32_MAX / 2 || b->rowsX > INT32_MAX / 2) return done(bfail(b, GDA_ERR_INVALID, "batch too large"));
+  if (b->rowsJ > INT32_MAX / 2 || b->rowsX > INT32_MAX / 2 || n_flags > INT32_MAX / 2)
+    return done(bfail(b, GDA_ERR_INVALID, "batch too large"));
+  b->n_flags = int(n_flags);
   b->pitch = pitch;
   st = [&]() -> gda_status {
     BCK(balloc(&b->inst, n));
@@ -739,6 +865,10 @@ gda_status gda_batch_create(int32_t n, const int32_t* N, const int32_t* model, c
     BCK(balloc(&b->bestR, n));
     BCK(balloc(&b->step_base, 1));
     BCK(cudaMemset(b->step_base, 0, sizeof(unsigned)));
+    BCK(balloc(&b->flags, size_t(b->n_flags)));
+    BCK(cudaMemset(b->flags, 0, size_t(b->n_flags) * sizeof(unsigned)));
+    BCK(balloc(&b->base, size_t(off_base)));
+    BCK(cudaMemset(b->base, 0, size_t(off_base) * sizeof(float)));
     BCK(balloc(&b->err, 1));
     BCK(cudaMemset(b->err, 0, sizeof(int)));
     for (int k = 0; k < n; ++k) {
@@ -765,11 +895,10 @@ gda_status gda_batch_create(int32_t n, const int32_t* N, const int32_t* model, c
     if (!encode(&b->tmA, b->J16, pitch, int(b->rowsJ), 128) || !encode(&b->tmB128, b->ops, pitch, int(b->rowsX), 128) ||
         !encode(&b->tmB256, b->ops, pitch, int(b->rowsX), 256))
       return bfail(b, GDA_ERR_CUDA, "tensor map encoding failed");
-    for (int model = 0; model < 2; ++model)
-      for (int wi = 0; wi < 2; ++wi) {
-        gda_status s = build_plan(b, model, wi ? 256 : 128, &b->plan[model][wi]);
-        if (s != GDA_OK) return s;
-      }
+    for (int wi = 0; wi < 2; ++wi) {
+      gda_status s = build_plan(b, wi ? 256 : 128, &b->plan[wi]);
+      if (s != GDA_OK) return s;
+    }
     BCK(set_batch_attrs());
     BCK(cudaDeviceSynchronize());
     return GDA_OK;
@@ -789,6 +918,46 @@ gda_status gda_batch_set_tile(gda_batch* b, int32_t bn) {
   return GDA_OK;
 }
 
+gda_status gda_batch_set_params(gda_batch* b, int32_t k, const gda_params* p) {
+  if (!b || k < 0 || k >= b->n) return GDA_ERR_INVALID;
+  if (!p) {
+    b->own[k] = 0;
+    return GDA_OK;
+  }
+  if (!std::isfinite(p->eps) || !std::isfinite(p->rho_th) || !std::isfinite(p->beta0) || !std::isfinite(p->eps_hat) ||
+      !(p->rho_th > 0) || !(p->dt > 0) || !std::isfinite(p->dt))
+    return bfail(b, GDA_ERR_INVALID, "non-finite settings, dt <= 0 or rho_th <= 0");
+  BatchInst& I = b->host[k];
+  I.dt = float(p->dt);
+  I.eps = float(p->eps);
+  I.rho_th = float(p->rho_th);
+  I.beta0 = float(p->beta0);
+  I.eps_hat = float(p->eps_hat);
+  I.sq = float(std::sqrt(p->rho_th));
+  b->own[k] = 1;
+  return GDA_OK;
+}
+
+gda_status gda_batch_set_init_base(gda_batch* b, int32_t k, const float* base, int32_t on_device) {
+  if (!b || k < 0 || k >= b->n) return GDA_ERR_INVALID;
+  BatchInst& I = b->host[k];
+  if (!base) {
+    I.has_base = 0;
+    return GDA_OK;
+  }
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (I.cplx) {
+    BCK(cudaMemcpyAsync(b->base + I.off_base, base, size_t(2) * I.N * sizeof(float), kind, b->stream));
+  } else {  // real amplitudes: imaginary parts zero
+    BCK(cudaMemsetAsync(b->base + I.off_base, 0, size_t(2) * I.N * sizeof(float), b->stream));
+    BCK(cudaMemcpy2DAsync(b->base + I.off_base, 2 * sizeof(float), base, sizeof(float), sizeof(float), I.N, kind,
+                          b->stream));
+  }
+  BCK(cudaStreamSynchronize(b->stream));
+  I.has_base = 1;
+  return GDA_OK;
+}
+
 gda_status gda_batch_run(gda_batch* b, const gda_params* p, int64_t steps) {
   if (!b || !p) return GDA_ERR_INVALID;
   if (steps < 0) return bfail(b, GDA_ERR_INVALID, "steps < 0");
@@ -796,28 +965,37 @@ gda_status gda_batch_run(gda_batch* b, const gda_params* p, int64_t steps) {
     return bfail(b, GDA_ERR_UNSUPPORTED, "batched runs are BF16 forward Euler");
   if (p->noise_D != 0.0 && p->noise_decay)
     return bfail(b, GDA_ERR_UNSUPPORTED, "batched runs support noise without decay only");
-  if (!(p->dt > 0) || !(p->rho_th > 0) || p->init_mode < 0 || p->init_mode > 2)
+  if (!(p->dt > 0) || !(p->rho_th > 0) || p->init_mode < 0 || p->init_mode > 3 || !std::isfinite(p->wait_s) ||
+      p->wait_s < 0 || p->wait_s > 1e3)
     return bfail(b, GDA_ERR_INVALID, "bad parameters");
   if (p->init_mode == 2 && !b->have_state) return bfail(b, GDA_ERR_STATE, "nothing to continue");
+  gda_status us = upload_settings(b, p);
+  if (us != GDA_OK) return us;
   if (p->init_mode != 2) {
     int maxRN = 1;
     for (auto& I : b->host) maxRN = std::max(maxRN, I.R * I.N);
     dim3 grid(std::min(1024, (maxRN + 255) / 256), b->n);
     k_batch_init<<<grid, 256, 0, b->stream>>>(b->inst, b->n, b->psi, b->gam, b->beta, b->h1, b->g64, b->off_g,
-                                              b->ops, b->pitch, p->init_mode, float(p->init_amp), float(p->gamma0),
-                                              float(p->beta0), float(std::sqrt(p->rho_th)));
+                                              b->base, b->ops, b->pitch, p->init_mode, float(p->init_amp),
+                                              float(p->gamma0));
     BCK(cudaGetLastError());
     BCK(cudaMemsetAsync(b->step_base, 0, sizeof(unsigned), b->stream));
+    BCK(cudaMemsetAsync(b->flags, 0, size_t(b->n_flags) * sizeof(unsigned), b->stream));
     b->step = 0;
     b->have_state = true;
   }
-  // Chunks of up to 100 steps replay one captured graph; the graph's kernels
-  // read the step index and buffer parity from the device counter.
+  // Chunks of `chunk` steps: one persistent launch each, replayed from a
+  // captured graph (launch + step counter advance); the kernel reads the step
+  // index and buffer parity from the device counter.
   const int chunk = 100;
-  const unsigned key[8] = {unsigned(b->bn), unsigned(float(p->dt) * 1e6f), unsigned(float(p->eps) * 1e6f),
-                           unsigned(float(p->rho_th) * 1e6f), unsigned(float(p->eps_hat) * 1e6f),
-                           unsigned(float(p->noise_D) * 1e6f), 0u, 0u};
-  if (steps >= chunk && (!b->graph || std::memcmp(key, b->graph_key, sizeof(key)) != 0)) {
+  float ws = float(p->wait_s);
+  unsigned wbits = 0;
+  std::memcpy(&wbits, &ws, sizeof(wbits));
+  float nd = float(p->noise_D);
+  unsigned nbits = 0;
+  std::memcpy(&nbits, &nd, sizeof(nbits));
+  const unsigned key[8] = {unsigned(b->bn), nbits, wbits, unsigned(chunk), 0u, 0u, 0u, 0u};
+  if (steps >= chunk && !b->graph_failed && (!b->graph || std::memcmp(key, b->graph_key, sizeof(key)) != 0)) {
     if (b->graph) {
       cudaGraphExecDestroy(b->graph);
       b->graph = nullptr;
@@ -827,30 +1005,46 @@ gda_status gda_batch_run(gda_batch* b, const gda_params* p, int64_t steps) {
     cudaStream_t saved = b->stream;
     b->stream = cap;
     BCK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
-    gda_status s = GDA_OK;
-    for (int k = 0; k < chunk && s == GDA_OK; ++k) s = launch_step(b, p, unsigned(k));
+    gda_status s = launch_chunk(b, p, 0u, chunk);
     k_batch_advance<<<1, 1, 0, cap>>>(b->step_base, unsigned(chunk));
     cudaGraph_t g = nullptr;
     const cudaError_t ce = cudaStreamEndCapture(cap, &g);
     b->stream = saved;
     cudaStreamDestroy(cap);
-    if (s != GDA_OK) return s;
-    BCK(ce);
-    BCK(cudaGraphInstantiate(&b->graph, g, 0));
-    cudaGraphDestroy(g);
-    std::memcpy(b->graph_key, key, sizeof(key));
+    cudaError_t ie = cudaErrorUnknown;
+    if (s == GDA_OK && ce == cudaSuccess) ie = cudaGraphInstantiate(&b->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (ie != cudaSuccess) {  // the driver does not capture this launch: chunks launch directly
+      cudaGetLastError();
+      b->graph = nullptr;
+      b->graph_failed = true;
+    } else {
+      std::memcpy(b->graph_key, key, sizeof(key));
+    }
   }
   int64_t done = 0;
-  for (; done + chunk <= steps; done += chunk) BCK(cudaGraphLaunch(b->graph, b->stream));
-  for (int64_t k = done; k < steps; ++k) {
-    gda_status s = launch_step(b, p, 0u);
+  for (; done + chunk <= steps; done += chunk) {
+    if (b->graph) {
+      BCK(cudaGraphLaunch(b->graph, b->stream));
+    } else {
+      gda_status s = launch_chunk(b, p, 0u, chunk);
+      if (s != GDA_OK) return s;
+      k_batch_advance<<<1, 1, 0, b->stream>>>(b->step_base, unsigned(chunk));
+      BCK(cudaGetLastError());
+    }
+  }
+  if (done < steps) {
+    const int rest = int(steps - done);
+    gda_status s = launch_chunk(b, p, 0u, rest);
     if (s != GDA_OK) return s;
-    k_batch_advance<<<1, 1, 0, b->stream>>>(b->step_base, 1u);
+    k_batch_advance<<<1, 1, 0, b->stream>>>(b->step_base, unsigned(rest));
     BCK(cudaGetLastError());
   }
   b->step += steps;
   return GDA_OK;
 }
+
+int32_t gda_batch_launch_mode(const gda_batch* b) { return !b ? -1 : (b->graph ? 1 : 0); }
 
 gda_status gda_batch_best(gda_batch* b, double* E, int32_t* r) {
   if (!b) return GDA_ERR_INVALID;
@@ -900,13 +1094,13 @@ const char* gda_batch_last_error(const gda_batch* b) { return b ? b->msg.c_str()
 void gda_batch_destroy(gda_batch* b) {
   if (!b) return;
   if (b->graph) cudaGraphExecDestroy(b->graph);
-  for (auto& row : b->plan)
-    for (auto& P : row) {
-      if (P.units) cudaFree(P.units);
-      if (P.cta_begin) cudaFree(P.cta_begin);
-    }
+  for (auto& P : b->plan) {
+    if (P.units) cudaFree(P.units);
+    if (P.cta_begin) cudaFree(P.cta_begin);
+  }
   void* ptrs[] = {b->inst, b->J16, b->ops, b->J64, b->g64, b->off_J, b->off_g, b->psi, b->gam, b->h1, b->beta,
-                  b->part, b->off_part, b->E_all, b->off_E, b->bestE, b->bestR, b->eunits, b->step_base, b->err};
+                  b->part, b->off_part, b->E_all, b->off_E, b->bestE, b->bestR, b->eunits, b->step_base, b->err,
+                  b->flags, b->base};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete b;

@@ -73,6 +73,9 @@ SIGNATURES = {
     "gda_batch_set_stream": (ct.c_int, [_VP, _VP]),
     "gda_batch_set_tile": (ct.c_int, [_VP, ct.c_int32]),
     "gda_batch_run": (ct.c_int, [_VP, ct.POINTER(Params), ct.c_int64]),
+    "gda_batch_set_params": (ct.c_int, [_VP, ct.c_int32, ct.POINTER(Params)]),
+    "gda_batch_set_init_base": (ct.c_int, [_VP, ct.c_int32, _VP, ct.c_int32]),
+    "gda_batch_launch_mode": (ct.c_int32, [_VP]),
     "gda_batch_best": (ct.c_int, [_VP, _D, ct.POINTER(ct.c_int32)]),
     "gda_batch_get_state": (ct.c_int, [_VP, ct.c_int32, _F, _F, _F]),
     "gda_batch_last_error": (ct.c_char_p, [_VP]),
@@ -349,6 +352,26 @@ class Batch:
 
     def run(self, params: Params, steps: int):
         self._check(self._lib.gda_batch_run(self._h, ct.byref(params), int(steps)))
+
+    def set_params(self, k: int, params: Params | None):
+        """Instance k's own eps, rho_th, beta0, eps_hat (None: follow each run's)."""
+        self._check(self._lib.gda_batch_set_params(self._h, int(k), None if params is None else ct.byref(params)))
+
+    def set_init_base(self, k: int, base: np.ndarray | None):
+        """Per-spin base amplitudes [N_k] (real or complex) of instance k for init_mode 3."""
+        if base is None:
+            self._check(self._lib.gda_batch_set_init_base(self._h, int(k), None, 0))
+            return
+        base = np.asarray(base)
+        if self.model[k] == XY:
+            flat = np.stack([base.real, base.imag], axis=-1).astype(np.float32).ravel()
+        else:
+            flat = np.ascontiguousarray(base.real, dtype=np.float32)
+        self._check(self._lib.gda_batch_set_init_base(self._h, int(k), flat.ctypes.data_as(_VP), 0))
+
+    def launch_mode(self) -> int:
+        """1: chunks replay a captured CUDA graph; 0: direct launches."""
+        return int(self._lib.gda_batch_launch_mode(self._h))
 
     def best(self):
         E = np.empty(self.n, dtype=np.float64)

@@ -98,6 +98,18 @@ class Proposal:
         return settings
 
 
+def propose_into_batch(prop: "Proposal", solver: "gda.Solver", batch: "gda.Batch", k: int, dt: float) -> dict:
+    """The proposal for the instance of `solver`, given to instance k of a
+    batch: its settings (gda_batch_set_params, with the batch step dt) and
+    its init_mode-3 base amplitudes.  Returns the settings."""
+    O = prop.outputs(solver)
+    settings = settings_from_outputs(O[:, 2:5].mean(0))
+    xy = solver.model == gda.XY
+    batch.set_init_base(k, AMP * (O[:, 0] + (1j * O[:, 1] if xy else 0.0)))
+    batch.set_params(k, run_params(settings, dt=dt))
+    return settings
+
+
 def proposed_params(settings: dict, seed: int, **kw) -> gda.Params:
     """Run parameters of a proposed start (init_mode 3, perturbation AMP)."""
     return run_params(settings, init_mode=3, init_amp=AMP, seed=seed, **kw)

@@ -119,3 +119,63 @@ def test_batch_rejects_unsupported(gda):
     with pytest.raises(gda.GdaError):
         b.run(gda.default_params(prec=gda.BF16, integ=gda.RK4), 5)
     b.close()
+
+
+def test_batch_own_settings_and_start_equal_single_instance_runs(gda):
+    """Instances with their own dt, eps, rho_th, ramp (gda_batch_set_params) and
+    base amplitudes (gda_batch_set_init_base, init_mode 3) follow exactly the
+    single-instance runs with those settings and that start."""
+    insts = mix(gda)[:5]
+    b = gda.Batch(insts, seed=77)
+    own = {0: dict(dt=0.05, eps=0.3, rho_th=1.2, beta0=0.6, eps_hat=0.2),
+           3: dict(dt=0.03, eps=0.05, rho_th=0.8, beta0=1.0, eps_hat=0.0)}
+    rng = np.random.default_rng(3)
+    bases = {}
+    for k in (0, 1, 4):
+        n = insts[k][0].shape[0]
+        xy = insts[k][2] == gda.XY
+        bases[k] = 0.1 * (rng.normal(size=n) + (1j * rng.normal(size=n) if xy else 0.0))
+        b.set_init_base(k, bases[k])
+    for k, st in own.items():
+        b.set_params(k, gda.default_params(**st))
+    run = dict(dt=0.05, eps=0.2, rho_th=1.0, beta0=0.4, eps_hat=0.3, noise_D=0.02, init_amp=0.05, prec=gda.BF16)
+    b.run(gda.default_params(init_mode=3, **run), 130)
+    for k, (J, g, model, R) in enumerate(insts):
+        kw = dict(run, **own.get(k, {}))
+        s = gda.Solver(J, g, model)
+        if k in bases:
+            s.set_init_base(bases[k])
+        s.run(gda.default_params(seed=b.instance_seed(k), schedule=gda.PER_STEP, init_mode=3 if k in bases else 1,
+                                 **kw), R, 130)
+        psi, gam, beta, _ = s.get_state()
+        bpsi, bgam, bbeta = b.get_state(k)
+        assert np.array_equal(psi, bpsi), k
+        assert np.array_equal(gam, bgam) and np.array_equal(beta, bbeta), k
+        s.close()
+    # back to the run's settings for instance 0
+    b.set_params(0, None)
+    b.run(gda.default_params(init_mode=1, **run), 10)
+    J, g, model, R = insts[0]
+    s = gda.Solver(J, g, model)
+    s.run(gda.default_params(seed=b.instance_seed(0), schedule=gda.PER_STEP, init_mode=1, **run), R, 10)
+    assert np.array_equal(s.get_state()[0], b.get_state(0)[0])
+    s.close()
+    b.close()
+
+
+def test_batch_continuation_across_chunks(gda):
+    """A batched run split into calls of 70, 100 and 33 steps (partial chunks,
+    a replayed chunk) equals one call of 203 steps."""
+    insts = mix(gda)[:4]
+    kw = dict(dt=0.05, eps=0.2, noise_D=0.01, init_amp=0.2, prec=gda.BF16)
+    a = gda.Batch(insts, seed=4)
+    a.run(gda.default_params(init_mode=1, **kw), 203)
+    b = gda.Batch(insts, seed=4)
+    b.run(gda.default_params(init_mode=1, **kw), 70)
+    b.run(gda.default_params(init_mode=2, **kw), 100)
+    b.run(gda.default_params(init_mode=2, **kw), 33)
+    for k in range(len(insts)):
+        assert np.array_equal(a.get_state(k)[0], b.get_state(k)[0]), k
+    assert a.launch_mode() in (0, 1)
+    a.close()
+    b.close()
