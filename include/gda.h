@@ -386,8 +386,9 @@ gda_status gda_adam_step(float* params, const float* grad, float* m1, float* m2,
  * Many independent instances (own N, model and R each) stepped together: one
  * persistent cooperative tensor-core launch runs a chunk of 100 steps of
  * every instance (both model types) over all their 128 x BN output tiles,
- * with steps ordered by per-tile dataflow flags; chunks replay from a captured
- * CUDA graph where the driver captures the launch (gda_batch_launch_mode).
+ * with steps ordered by per-tile dataflow flags (or, by choice, one launch per
+ * step: gda_batch_set_schedule); chunks replay from a captured CUDA graph
+ * where the driver captures the launch (gda_batch_launch_mode).
  * Every instance follows exactly the single-instance forward-Euler BF16
  * dynamics (Eqs. 2, 5, 6) with its own Philox seed and, optionally, its own
  * settings and start (gda_batch_set_params, gda_batch_set_init_base).  The
@@ -406,6 +407,13 @@ gda_status gda_batch_set_stream(gda_batch* b, void* stream);
 /* Tile width of the coupling product: 128 or 256 columns (the caller times
  * both and keeps the faster). */
 gda_status gda_batch_set_tile(gda_batch* b, int32_t bn);
+
+/* Launch schedule of the batch: GDA_SCHEDULE_RESIDENT (the default) runs each
+ * chunk of 100 steps as one persistent launch with steps ordered by per-tile
+ * flags; GDA_SCHEDULE_PER_STEP launches every step separately (the kernel
+ * boundary orders the steps).  Same numbers either way; which is faster
+ * depends on the mix (the caller times both).  GDA_ERR_INVALID otherwise. */
+gda_status gda_batch_set_schedule(gda_batch* b, int32_t schedule);
 
 /* Runs `steps` forward-Euler BF16 steps of every instance (p->integ must be
  * GDA_EULER, p->prec GDA_BF16; noise without decay; init_mode 0, 1, 2 or 3;

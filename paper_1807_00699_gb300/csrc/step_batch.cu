@@ -27,6 +27,7 @@
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/gda.h"
@@ -150,6 +151,9 @@ __device__ __forceinline__ bool epi_unit(const BatchArgs& b, const BatchInst& I,
   const int i = m0 + 32 * q + lane;
   const int cbeg = n0 + part * PW;
   const unsigned* fl = b.flags + I.flag0 + U.nt * I.mt;
+  constexpr int PF = ModeTraits<M_EULER>::l2_ahead;  // chunks pulled into L2 ahead of their loads
+#pragma unroll
+  for (int p = 1; p <= PF && p < NCH; ++p) epi_prefetch_l2<M_EULER, CPLX, CW>(a, i, cbeg + p * CW, lane);
   EpiRegs<M_EULER, CPLX, CW> R[2];
   epi_load<M_EULER, CPLX, CW>(a, i, cbeg, R[0]);  // own rows of psi and gamma: written by this thread
   bool fok = true;
@@ -171,6 +175,7 @@ __device__ __forceinline__ bool epi_unit(const BatchArgs& b, const BatchInst& I,
   }
   const uint32_t taddr = tacc + (static_cast<uint32_t>(32 * q) << 16) + part * PW;
   auto body = [&](int ch, const EpiRegs<M_EULER, CPLX, CW>& cr, EpiRegs<M_EULER, CPLX, CW>& nx) {
+    if (ch + 1 + PF < NCH) epi_prefetch_l2<M_EULER, CPLX, CW>(a, i, cbeg + (ch + 1 + PF) * CW, lane);
     if (ch + 1 < NCH) epi_load<M_EULER, CPLX, CW>(a, i, cbeg + (ch + 1) * CW, nx);
     float v[CW];
     tmem_ld<CW>(taddr + ch * CW, v);
@@ -193,16 +198,13 @@ __device__ __forceinline__ bool epi_unit(const BatchArgs& b, const BatchInst& I,
     if (r < a.R) a.beta_out[r] = next_beta(a, a.beta_in[r]);
   }
   bar_epi();
-  if (e == 0) {
-    __threadfence();
+  if (e == 0)  // a release store: ordered after every epilogue thread's writes (seen through the barrier)
     st_release_gpu(b.flags + I.flag0 + U.nt * I.mt + U.mt, step + 1u);
-  }
   return true;
 }
 
-// 112 registers a thread: 576 x 112 fill the SM's register file, one CTA per SM.
 template <int BN, int STAGES>
-__global__ void __maxnreg__(112)
+__global__ void __launch_bounds__(NTHREADS, 1)
     step_batch_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, BatchArgs b) {
   using Cfg = BCfg<BN, STAGES>;
   extern __shared__ uint8_t smem_raw[];
@@ -587,6 +589,7 @@ struct gda_batch {
   CUtensorMap tmA{}, tmB128{}, tmB256{};
   BatchPlan plan[2];     // [width: 128, 256], units of both model types
   int bn = 128;          // tile width in use (autotuned)
+  bool persistent = true;  // one launch per chunk of steps (else one launch per step)
   std::vector<char> own;  // instance k has its own settings (gda_batch_set_params)
   std::vector<BatchInst> uploaded;  // the instance table as last copied to the device
   unsigned long long step = 0;
@@ -648,6 +651,11 @@ gda_status build_plan(gda_batch* b, int bn, BatchPlan* P) {
     bins[best].push_back(u);
     load[best] += cost[u];
   }
+  // within a CTA, units in one global order (instance, column block, row
+  // block): a unit of the next step then depends on tiles every CTA finished
+  // early in this step
+  auto key = [&](int u) { return std::make_tuple(units[u].inst, units[u].nt, units[u].mt); };
+  for (auto& bin : bins) std::sort(bin.begin(), bin.end(), [&](int x, int y) { return key(x) < key(y); });
   std::vector<BatchUnit> flat;
   std::vector<int> begin(P->grid + 1, 0);
   for (int c = 0; c < P->grid; ++c) {
@@ -918,6 +926,12 @@ gda_status gda_batch_set_tile(gda_batch* b, int32_t bn) {
   return GDA_OK;
 }
 
+gda_status gda_batch_set_schedule(gda_batch* b, int32_t schedule) {
+  if (!b || (schedule != GDA_SCHEDULE_RESIDENT && schedule != GDA_SCHEDULE_PER_STEP)) return GDA_ERR_INVALID;
+  b->persistent = schedule == GDA_SCHEDULE_RESIDENT;
+  return GDA_OK;
+}
+
 gda_status gda_batch_set_params(gda_batch* b, int32_t k, const gda_params* p) {
   if (!b || k < 0 || k >= b->n) return GDA_ERR_INVALID;
   if (!p) {
@@ -994,7 +1008,7 @@ gda_status gda_batch_run(gda_batch* b, const gda_params* p, int64_t steps) {
   float nd = float(p->noise_D);
   unsigned nbits = 0;
   std::memcpy(&nbits, &nd, sizeof(nbits));
-  const unsigned key[8] = {unsigned(b->bn), nbits, wbits, unsigned(chunk), 0u, 0u, 0u, 0u};
+  const unsigned key[8] = {unsigned(b->bn), nbits, wbits, unsigned(chunk), unsigned(b->persistent), 0u, 0u, 0u};
   if (steps >= chunk && !b->graph_failed && (!b->graph || std::memcmp(key, b->graph_key, sizeof(key)) != 0)) {
     if (b->graph) {
       cudaGraphExecDestroy(b->graph);
@@ -1005,7 +1019,12 @@ gda_status gda_batch_run(gda_batch* b, const gda_params* p, int64_t steps) {
     cudaStream_t saved = b->stream;
     b->stream = cap;
     BCK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
-    gda_status s = launch_chunk(b, p, 0u, chunk);
+    gda_status s = GDA_OK;
+    if (b->persistent) {
+      s = launch_chunk(b, p, 0u, chunk);
+    } else {
+      for (int k = 0; k < chunk && s == GDA_OK; ++k) s = launch_chunk(b, p, unsigned(k), 1);
+    }
     k_batch_advance<<<1, 1, 0, cap>>>(b->step_base, unsigned(chunk));
     cudaGraph_t g = nullptr;
     const cudaError_t ce = cudaStreamEndCapture(cap, &g);
@@ -1026,17 +1045,21 @@ gda_status gda_batch_run(gda_batch* b, const gda_params* p, int64_t steps) {
   for (; done + chunk <= steps; done += chunk) {
     if (b->graph) {
       BCK(cudaGraphLaunch(b->graph, b->stream));
-    } else {
-      gda_status s = launch_chunk(b, p, 0u, chunk);
-      if (s != GDA_OK) return s;
-      k_batch_advance<<<1, 1, 0, b->stream>>>(b->step_base, unsigned(chunk));
-      BCK(cudaGetLastError());
+      continue;
     }
+    for (int k = 0; k < (b->persistent ? 1 : chunk); ++k) {
+      gda_status s = launch_chunk(b, p, unsigned(k), b->persistent ? chunk : 1);
+      if (s != GDA_OK) return s;
+    }
+    k_batch_advance<<<1, 1, 0, b->stream>>>(b->step_base, unsigned(chunk));
+    BCK(cudaGetLastError());
   }
   if (done < steps) {
     const int rest = int(steps - done);
-    gda_status s = launch_chunk(b, p, 0u, rest);
-    if (s != GDA_OK) return s;
+    for (int k = 0; k < (b->persistent ? 1 : rest); ++k) {
+      gda_status s = launch_chunk(b, p, unsigned(k), b->persistent ? rest : 1);
+      if (s != GDA_OK) return s;
+    }
     k_batch_advance<<<1, 1, 0, b->stream>>>(b->step_base, unsigned(rest));
     BCK(cudaGetLastError());
   }

@@ -237,9 +237,12 @@ __global__ void __launch_bounds__(TcThreads<MODE>::N, 1)
     const int part = (warp - 2) >> 2;
     const bool need_red = MODE == M_ENERGY || ((MODE == M_EULER || MODE == M_RK4) && a.rho_out != nullptr);
     float* out = (MODE == M_ENERGY) ? a.e_part : ((MODE == M_EULER || MODE == M_RK4) ? a.rho_out : nullptr);
+    constexpr int PD = ModeTraits<MODE>::prefetch;  // chunks loaded ahead of the one computed
+    constexpr int NB = PD + 1;
+    constexpr int PF = ModeTraits<MODE>::l2_ahead;  // chunks pulled into L2 ahead of their loads
     int bad = 0;
     int lt = 0;
-    EpiRegs<MODE, CPLX, CW> R[2];
+    EpiRegs<MODE, CPLX, CW> R[NB];
     for (int t = unit0; t < T; t += nunit, ++lt) {
       const int m0 = tile_m0(t), n0 = (t % NT) * BN;
       const int mt = m0 / BM;
@@ -251,7 +254,12 @@ __global__ void __launch_bounds__(TcThreads<MODE>::N, 1)
       // FP8: the accumulator holds (J0_ij / s_i)(psi_j / sigma); one product
       // with s_i sigma restores Y (sigma a power of two: exact).
       const float rs = F8 ? __fmul_rn(a.row_scale[i], kFp8PsiScale) : 1.0f;
-      epi_load<MODE, CPLX, CW>(a, i, cbeg, R[0]);  // overlaps the MMAs
+      if (lt == 0) {  // later tiles had theirs pulled in during the previous tile
+#pragma unroll
+        for (int p = 0; p < PF && p < NCH; ++p) epi_prefetch_l2<MODE, CPLX, CW>(a, i, cbeg + p * CW, lane);
+      }
+#pragma unroll
+      for (int p = 0; p < PD && p < NCH; ++p) epi_load<MODE, CPLX, CW>(a, i, cbeg + p * CW, R[p]);  // overlaps the MMAs
       if (e < RPT) {
         const int r = rbase + e;
         const float bt = r < a.R ? a.beta_in[r] : 1.0f;
@@ -269,8 +277,7 @@ __global__ void __launch_bounds__(TcThreads<MODE>::N, 1)
       }
       if (lt == 0 && e == 0) stamp(a, 4);
       const uint32_t taddr = tmem + b * BN + (static_cast<uint32_t>(32 * q) << 16) + part * PW;
-      auto body = [&](int ch, const EpiRegs<MODE, CPLX, CW>& cur, EpiRegs<MODE, CPLX, CW>& nxt) {
-        if (ch + 1 < NCH) epi_load<MODE, CPLX, CW>(a, i, cbeg + (ch + 1) * CW, nxt);
+      auto body = [&](int ch, const EpiRegs<MODE, CPLX, CW>& cur) {
         float v[CW];
         tmem_ld<CW>(taddr + ch * CW, v);
         if (F8) {
@@ -290,12 +297,23 @@ __global__ void __launch_bounds__(TcThreads<MODE>::N, 1)
           }
         }
       };
-#pragma unroll 1
-      for (int ch = 0; ch + 1 < NCH; ch += 2) {
-        body(ch, R[0], R[1]);
-        body(ch + 1, R[1], R[0]);
+      // fully unrolled, so every register buffer index is a constant
+      // the next tile of this CTA: its first chunks are pulled into L2 during
+      // the last chunks of this one
+      const int tn = t + nunit;
+      const int i_next = tile_m0(tn) + 32 * q + lane;
+      const int cbeg_next = (tn % NT) * BN + part * PW;
+#pragma unroll
+      for (int ch = 0; ch < NCH; ++ch) {
+        if (PF > 0) {
+          if (ch + PF < NCH)
+            epi_prefetch_l2<MODE, CPLX, CW>(a, i, cbeg + (ch + PF) * CW, lane);
+          else if (tn < T && ch + PF - NCH < NCH)
+            epi_prefetch_l2<MODE, CPLX, CW>(a, i_next, cbeg_next + (ch + PF - NCH) * CW, lane);
+        }
+        if (ch + PD < NCH) epi_load<MODE, CPLX, CW>(a, i, cbeg + (ch + PD) * CW, R[(ch + PD) % NB]);
+        body(ch, R[ch % NB]);
       }
-      if (NCH & 1) body(NCH - 1, R[0], R[1]);
       tc_fence_before();
       epi_bar_sync_n<32 * NEPI>();
       if (e == 0) {  // accumulator b may be overwritten

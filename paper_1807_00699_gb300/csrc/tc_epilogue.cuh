@@ -18,6 +18,13 @@ struct ModeTraits {
   static constexpr bool rk_mid = MODE == M_RK2 || MODE == M_RK3 || MODE == M_RK4;
   static constexpr bool has_x = MODE != M_RAW;
   static constexpr bool has_g = MODE != M_RAW && MODE != M_ENERGY;
+  // chunks whose inputs are loaded into registers ahead of the one computed
+  // (a second chunk in registers spills at the 96 registers of a 576-thread
+  // block and measured slower)
+  static constexpr int prefetch = 1;
+  // chunks whose state lines are pulled into L2 ahead of their register
+  // loads (no registers: the loads of a chunk then find their lines in L2)
+  static constexpr int l2_ahead = MODE == M_RAW ? 0 : 3;
 };
 
 template <int MODE, bool CPLX, int CW>
@@ -65,6 +72,40 @@ __device__ __forceinline__ void epi_load(const StepArgs& a, int i, int c0, EpiRe
         R.gn[u] = a.gam[og];
         R.ga[u] = a.gacc[og];
       }
+    }
+  }
+}
+
+static __device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+// Pulls into L2 the state lines that epi_load of columns c0 .. c0+CW-1 will
+// read for the warp's 32 rows (i - lane .. i - lane + 31: one 128-byte line per
+// column): lanes 0 .. CW-1 take the amplitude columns, the next CW / W lanes
+// the gain rows.  Addresses are clamped as in epi_load.
+template <int MODE, bool CPLX, int CW>
+__device__ __forceinline__ void epi_prefetch_l2(const StepArgs& a, int i, int c0, int lane) {
+  using Tr = ModeTraits<MODE>;
+  constexpr int W = CPLX ? 2 : 1;
+  constexpr int NR = CW / W;
+  if (MODE == M_RAW) return;
+  const size_t Np = a.Np;
+  const int ib = i - lane;
+  if (lane < CW) {
+    const size_t o = size_t(min(c0 + lane, a.Cp - 1)) * Np + ib;
+    prefetch_l2((MODE == M_ENERGY ? a.psi_n : a.xs) + o);
+    if (Tr::rk_mid) {
+      prefetch_l2(a.psi_n + o);
+      prefetch_l2(a.acc + o);
+    }
+  } else if (Tr::has_g && lane < CW + NR) {
+    const int r0 = CPLX ? c0 / 2 : c0;
+    const size_t og = size_t(min(r0 + lane - CW, a.Rp - 1)) * Np + ib;
+    prefetch_l2(((MODE == M_EULER || MODE == M_RK1) ? a.gam : a.gstg) + og);
+    if (Tr::rk_mid) {
+      prefetch_l2(a.gam + og);
+      prefetch_l2(a.gacc + og);
     }
   }
 }

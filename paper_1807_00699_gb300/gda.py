@@ -72,6 +72,7 @@ SIGNATURES = {
                                     ct.POINTER(_VP), ct.POINTER(_VP), ct.c_uint64, ct.POINTER(_VP)]),
     "gda_batch_set_stream": (ct.c_int, [_VP, _VP]),
     "gda_batch_set_tile": (ct.c_int, [_VP, ct.c_int32]),
+    "gda_batch_set_schedule": (ct.c_int, [_VP, ct.c_int32]),
     "gda_batch_run": (ct.c_int, [_VP, ct.POINTER(Params), ct.c_int64]),
     "gda_batch_set_params": (ct.c_int, [_VP, ct.c_int32, ct.POINTER(Params)]),
     "gda_batch_set_init_base": (ct.c_int, [_VP, ct.c_int32, _VP, ct.c_int32]),
@@ -349,6 +350,10 @@ class Batch:
 
     def set_tile(self, bn: int):
         self._check(self._lib.gda_batch_set_tile(self._h, bn))
+
+    def set_schedule(self, schedule: int):
+        """RESIDENT: one persistent launch per 100 steps; PER_STEP: one launch per step."""
+        self._check(self._lib.gda_batch_set_schedule(self._h, schedule))
 
     def run(self, params: Params, steps: int):
         self._check(self._lib.gda_batch_run(self._h, ct.byref(params), int(steps)))

@@ -17,7 +17,7 @@ HEADER = os.path.join(ROOT, "include", "gda.h")
 
 @pytest.fixture(scope="module")
 def lib():
-    __graft_entry__.build()
+    __graft_entry__.ensure_built()
     return gda.load_library()
 
 

@@ -15,7 +15,7 @@ def gda():
 
     import __graft_entry__
     assert torch.cuda.is_available()
-    __graft_entry__.build()
+    __graft_entry__.ensure_built()
     from paper_1807_00699_gb300 import gda as mod
     return mod
 
@@ -179,3 +179,28 @@ def test_batch_continuation_across_chunks(gda):
     assert a.launch_mode() in (0, 1)
     a.close()
     b.close()
+
+
+def test_batch_schedules_agree(gda):
+    """One persistent launch per chunk (steps ordered by tile flags) and one
+    launch per step give the same bits, at both tile widths."""
+    insts = mix(gda)
+    kw = dict(dt=0.05, eps=0.2, eps_hat=0.1, beta0=0.5, noise_D=0.01, init_amp=0.2, prec=gda.BF16)
+    out = {}
+    for sched in (gda.RESIDENT, gda.PER_STEP):
+        for bn in (128, 256):
+            b = gda.Batch(insts, seed=21)
+            b.set_schedule(sched)
+            b.set_tile(bn)
+            b.run(gda.default_params(init_mode=1, **kw), 130)
+            out[(sched, bn)] = [b.get_state(k)[0] for k in range(len(insts))]
+            b.close()
+    ref = out[(gda.RESIDENT, 128)]
+    for key, states in out.items():
+        for k, (x, y) in enumerate(zip(ref, states)):
+            if key[1] == 128:
+                assert np.array_equal(x, y), (key, k)
+            else:  # another tile width sums the same products in another order
+                assert np.abs(x - y).max() <= 1e-5 * max(1.0, np.abs(x).max()), (key, k)
+    with pytest.raises(gda.GdaError):
+        gda.Batch(insts[:1], seed=1).set_schedule(gda.PAIR)

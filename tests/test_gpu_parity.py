@@ -22,7 +22,7 @@ def gda():
 
     import __graft_entry__
     assert torch.cuda.is_available()
-    __graft_entry__.build()
+    __graft_entry__.ensure_built()
     from paper_1807_00699_gb300 import gda as mod
     return mod
 

@@ -17,7 +17,7 @@ def env():
 
     import __graft_entry__
     assert torch.cuda.is_available()
-    __graft_entry__.build()
+    __graft_entry__.ensure_built()
     from paper_1807_00699_gb300 import gda
     return torch, gda, gda.load_library()
 

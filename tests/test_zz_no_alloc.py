@@ -20,7 +20,7 @@ MAX_R = 4096
 
 def _lib():
     import __graft_entry__
-    __graft_entry__.build()
+    __graft_entry__.ensure_built()
     from paper_1807_00699_gb300 import gda
     return gda, gda.load_library()
 
