@@ -134,7 +134,7 @@ __device__ __forceinline__ StepArgs unit_args(const BatchArgs& b, const BatchIns
 template <int BN, bool CPLX>
 __device__ __forceinline__ bool epi_unit(const BatchArgs& b, const BatchInst& I, const BatchUnit& U, unsigned step,
                                          int cur, int n, uint32_t tacc, uint32_t full, uint32_t empty, uint32_t use,
-                                         float* s_beta, float* s_dsc, int* s_flag, int& bad) {
+                                         float* s_beta, float* s_dsc, int* s_flag, StepArgs* s_args, int& bad) {
   constexpr int W = CPLX ? 2 : 1;
   constexpr int RPT = BN / W;
   constexpr int PW = BN / (NEPI / 4);  // columns per part
@@ -145,7 +145,12 @@ __device__ __forceinline__ bool epi_unit(const BatchArgs& b, const BatchInst& I,
   const int e = threadIdx.x - 64;
   const int q = warp & 3;
   const int part = (warp - 2) >> 2;
-  const StepArgs a = unit_args(b, I, step, cur);
+  // the unit's arguments live in shared memory (read where used), not in
+  // every epilogue thread's registers
+  bar_epi();  // every thread is done with the previous unit's arguments
+  if (e == 0) *s_args = unit_args(b, I, step, cur);
+  bar_epi();
+  const StepArgs& a = *s_args;
   const int m0 = U.mt * BM, n0 = U.nt * BN;
   const int rbase = n0 / W;
   const int i = m0 + 32 * q + lane;
@@ -189,17 +194,20 @@ __device__ __forceinline__ bool epi_unit(const BatchArgs& b, const BatchInst& I,
     body(ch + 1, R[1], R[0]);
   }
   if (NCH & 1) body(NCH - 1, R[0], R[1]);
+  const bool publish = b.nsteps > 1;  // later steps of this launch read what this unit wrote
   tc_fence_before();
-  fence_proxy_async_global();  // the next operand rows are read by other CTAs' TMA loads
+  if (publish) fence_proxy_async_global();  // the next operand rows are read by other CTAs' TMA loads
   bar_epi();
   if (e == 0) mbar_arrive(empty);
   if (e < RPT && U.mt == 0) {
     const int r = rbase + e;
     if (r < a.R) a.beta_out[r] = next_beta(a, a.beta_in[r]);
   }
-  bar_epi();
-  if (e == 0)  // a release store: ordered after every epilogue thread's writes (seen through the barrier)
-    st_release_gpu(b.flags + I.flag0 + U.nt * I.mt + U.mt, step + 1u);
+  if (publish) {
+    bar_epi();
+    if (e == 0)  // a release store: ordered after every epilogue thread's writes (seen through the barrier)
+      st_release_gpu(b.flags + I.flag0 + U.nt * I.mt + U.mt, step + 1u);
+  }
   return true;
 }
 
@@ -218,6 +226,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   float* s_dsc = s_beta + BN;
   uint32_t* s_tmem = reinterpret_cast<uint32_t*>(s_dsc + 5 * BN);
   int* s_flag = reinterpret_cast<int*>(s_tmem + 1);
+  __shared__ StepArgs s_args;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned step0 = *b.step_base + b.step_off;
@@ -348,9 +357,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const uint32_t use = lt >> 1;
         const uint32_t tacc = tmem + k2 * BN;
         run = I.cplx ? epi_unit<BN, true>(b, I, U, step, cur, n, tacc, acc_full(k2), acc_empty(k2), use, s_beta,
-                                          s_dsc, s_flag, bad)
+                                          s_dsc, s_flag, &s_args, bad)
                      : epi_unit<BN, false>(b, I, U, step, cur, n, tacc, acc_full(k2), acc_empty(k2), use, s_beta,
-                                           s_dsc, s_flag, bad);
+                                           s_dsc, s_flag, &s_args, bad);
       }
     }
     if (bad) s_flag[1] = 1;

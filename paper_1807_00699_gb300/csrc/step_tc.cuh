@@ -126,6 +126,7 @@ __global__ void __launch_bounds__(TcThreads<MODE>::N, 1)
   if (warp == 0) {
     // ---------------- TMA producer ----------------
     if (lane == 0) {
+      const uint64_t keep = policy_evict_last();  // J and the operand are re-read by every tile row / column
       int it = 0;
       bool stop = false;
       for (int t = unit0; t < T && !stop; t += nunit) {
@@ -140,12 +141,12 @@ __global__ void __launch_bounds__(TcThreads<MODE>::N, 1)
           if (PAIR) {
             const uint32_t fb = mapa_shared(full_bar(s), 0);  // the even CTA counts both CTAs' bytes
             if (leader) mbar_arrive_expect_tx(full_bar(s), 2 * Cfg::STAGE_BYTES);
-            tma_load_2d_pair(sA + s * Cfg::A_BYTES, &tmA, kb * BKE, m0, fb);
-            tma_load_2d_pair(sB + s * Cfg::B_BYTES, &tmB, kb * BKE, b_row0 + n0, fb);
+            tma_load_2d_pair_hint(sA + s * Cfg::A_BYTES, &tmA, kb * BKE, m0, fb, keep);
+            tma_load_2d_pair_hint(sB + s * Cfg::B_BYTES, &tmB, kb * BKE, b_row0 + n0, fb, keep);
           } else {
             mbar_arrive_expect_tx(full_bar(s), Cfg::STAGE_BYTES);
-            tma_load_2d(sA + s * Cfg::A_BYTES, &tmA, kb * BKE, m0, full_bar(s));
-            tma_load_2d(sB + s * Cfg::B_BYTES, &tmB, kb * BKE, b_row0 + n0, full_bar(s));
+            tma_load_2d_hint(sA + s * Cfg::A_BYTES, &tmA, kb * BKE, m0, full_bar(s), keep);
+            tma_load_2d_hint(sB + s * Cfg::B_BYTES, &tmB, kb * BKE, b_row0 + n0, full_bar(s), keep);
           }
         }
       }

@@ -134,7 +134,8 @@ def ttt_steps(steps, E, target):
 def make_targets(J, g, xy, R=32, nsteps=1500, every=50, seed=1):
     """Runs the plain GD algorithm with every candidate setting; returns the
     best configuration found (unit spins, [N][2]) and the candidate setting that
-    first reaches within 1e-3 of the best energy (ties: lower final energy)."""
+    first reaches within 1e-3 of the best energy (ties: lower final energy),
+    judged on the FP64 energies of the traced configurations."""
     s = gda.Solver(J, g, gda.XY if xy else gda.ISING)
     runs = []
     for (eps, rho, b0) in GRID:
@@ -142,8 +143,8 @@ def make_targets(J, g, xy, R=32, nsteps=1500, every=50, seed=1):
                        prec=gda.BF16, energy_every=every)
         s.run(p, R, nsteps)
         E, r, cfg = s.best()
-        st, Et, _ = s.trace()
-        runs.append((E, cfg, st, Et))
+        st, _, _ = s.trace()
+        runs.append((E, cfg, st, s.trace_energy()))  # FP64 energies of the traced configurations
     s.close()
     Ebest = min(x[0] for x in runs)
     target = Ebest + 1e-3 * abs(Ebest)
@@ -234,44 +235,95 @@ def train(n_inst=384, epochs=40, batch=16, lr=2e-3, wset=0.5, seed=0, log=print)
     return p.cpu().numpy(), losses
 
 
-def evaluate(prop: Proposal, cases, R=64, nsteps=5000, every=25, log=print):
-    """Time to target of plain GD (default settings, small random start) and of
-    the proposal (its settings and start), BF16, same R and steps; the target
-    is within 1e-3 of the better FP64 energy of the two runs."""
-    import synth
+def _run_fp64(solver, params, R, nsteps):
+    """One run with the energy trace: (trace steps, FP64 energies of the
+    configurations the trace names, FP64 energies of every restart at the end,
+    seconds)."""
     import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    solver.run(params, R, nsteps)
+    e1.record()
+    e1.synchronize()
+    st, _, _ = solver.trace()
+    return st, solver.trace_energy(), solver.energy(), e0.elapsed_time(e1) / 1e3
+
+
+def _first_hit(st, E64, target):
+    hit = np.nonzero(E64 <= target)[0]
+    return int(st[hit[0]]) if len(hit) else None
+
+
+def eval_instance(model: str, n: int, seed: int):
+    """Held-out instance of the evaluation: J ~ N(0, 1/N), g ~ U[-0.1, 0.1] (XY) or 0 (Ising)."""
+    import synth
+    J, g = synth.xy_gaussian(n, seed)
+    return J, (g if model == "xy" else np.zeros(n))
+
+
+def best_fixed_setting(model: str, n: int, seeds, R=64, nsteps=5000, every=25, dt=0.05, log=print) -> tuple:
+    """The grid setting (eps, rho_th, beta0) that reaches its instances' targets
+    fastest (FP64-verified), on calibration instances of the same family that
+    the evaluation does not use: most hits first, then fewest steps."""
+    score = {k: [] for k in range(len(GRID))}
+    for seed in seeds:
+        J, g = eval_instance(model, n, seed)
+        s = gda.Solver(J, g, gda.XY if model == "xy" else gda.ISING)
+        runs = {}
+        for k, (e, rho, b0) in enumerate(GRID):
+            prm = run_params({"eps": e, "rho_th": rho, "beta0": b0}, dt=dt, init_mode=1, init_amp=1e-3, seed=seed,
+                             prec=gda.BF16, energy_every=every)
+            runs[k] = _run_fp64(s, prm, R, nsteps)
+        s.close()
+        Estar = min(min(float(r[1].min()), float(r[2].min())) for r in runs.values())
+        target = Estar + 1e-3 * abs(Estar)
+        for k, r in runs.items():
+            h = _first_hit(r[0], r[1], target)
+            score[k].append(h if h is not None else 10 ** 9)
+    k_best = min(score, key=lambda k: (sum(x >= 10 ** 9 for x in score[k]), float(np.mean(score[k]))))
+    log({"model": model, "N": n, "calibration": {str(GRID[k]): v for k, v in score.items()}, "best": GRID[k_best]})
+    return GRID[k_best]
+
+
+def evaluate(prop: Proposal, cases, R=64, nsteps=5000, every=25, fixed=None, log=print):
+    """FP64-verified time to target of three arms on held-out seeds, BF16, same
+    R and steps: plain GD (default settings, small random start), plain GD at
+    the best fixed grid setting for the model (fixed[model], from
+    best_fixed_setting), and the proposal (its settings and start).  The
+    target is within 1e-3 of the best FP64 energy any arm reached (final
+    restarts or traced configurations); an arm hits it at the first trace
+    point whose named configuration is at or below it in FP64."""
     rows = []
     for model, n, seed in cases:
-        J, g = synth.xy_gaussian(n, seed)
+        J, g = eval_instance(model, n, seed)
         xy = model == "xy"
-        if not xy:
-            g = np.zeros(n)
         s = gda.Solver(J, g, gda.XY if xy else gda.ISING)
         res = {}
-        for arm in ("plain", "learned"):
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            torch.cuda.synchronize()
-            e0.record()
+        arms = ["plain", "learned"] + (["best_fixed"] if fixed else [])
+        for arm in arms:
             if arm == "plain":
-                s.run(gda.default_params(dt=0.05, eps=0.1, rho_th=1.0, init_mode=1, init_amp=1e-3, seed=seed,
-                                         prec=gda.BF16, energy_every=every), R, nsteps)
                 settings = {"eps": 0.1, "rho_th": 1.0, "beta0": 1.0}
+                prm = gda.default_params(dt=0.05, eps=0.1, rho_th=1.0, init_mode=1, init_amp=1e-3, seed=seed,
+                                         prec=gda.BF16, energy_every=every)
+            elif arm == "best_fixed":
+                e, rho, b0 = fixed[model]
+                settings = {"eps": e, "rho_th": rho, "beta0": b0}
+                prm = run_params(settings, dt=0.05, init_mode=1, init_amp=1e-3, seed=seed, prec=gda.BF16,
+                                 energy_every=every)
             else:
                 settings = prop.propose(s)
-                s.run(proposed_params(settings, seed, dt=0.05, prec=gda.BF16, energy_every=every), R, nsteps)
-            E, _, _ = s.best(with_cfg=False)
-            e1.record()
-            e1.synchronize()
-            st_, Et, _ = s.trace()
-            res[arm] = (E, st_, Et, e0.elapsed_time(e1) / 1e3, settings)
-        Estar = min(res["plain"][0], res["learned"][0])
+                prm = proposed_params(settings, seed, dt=0.05, prec=gda.BF16, energy_every=every)
+            st_, E64, E_all, sec = _run_fp64(s, prm, R, nsteps)
+            res[arm] = (E64, E_all, st_, sec, settings)
+        Estar = min(min(float(r[0].min()), float(r[1].min())) for r in res.values())
         target = Estar + 1e-3 * abs(Estar)
         row = {"model": model, "N": n, "seed": seed, "E_star": Estar}
-        for arm, (E, st_, Et, sec, settings) in res.items():
-            k = ttt_steps(st_, Et, target)
-            row[arm] = {"E": E, "ttt_steps": k, "ttt_s": None if k is None else sec * k / nsteps, "run_s": sec,
-                        "settings": settings}
+        for arm, (E64, E_all, st_, sec, settings) in res.items():
+            k = _first_hit(st_, E64, target)
+            row[arm] = {"E": float(E_all.min()), "ttt_steps": k, "ttt_s": None if k is None else sec * k / nsteps,
+                        "run_s": sec, "settings": settings}
         rows.append(row)
         log(row)
         s.close()
@@ -297,8 +349,10 @@ def main(argv=None):
         report = {"losses": losses}
     else:
         prop = Proposal(np.load(a.out))
+        fixed = {"xy": best_fixed_setting("xy", 1024, [2 * 10 ** 6, 2 * 10 ** 6 + 1]),
+                 "ising": best_fixed_setting("ising", 2048, [2 * 10 ** 6 + 100, 2 * 10 ** 6 + 101])}
         cases = [("xy", 1024, 10 ** 6 + k) for k in range(4)] + [("ising", 2048, 10 ** 6 + 100 + k) for k in range(4)]
-        report = {"eval": evaluate(prop, cases)}
+        report = {"best_fixed": fixed, "eval": evaluate(prop, cases, fixed=fixed)}
     if a.report:
         with open(a.report, "w") as fh:
             json.dump(report, fh, indent=1, default=float)
