@@ -163,7 +163,7 @@ typedef enum {
   GDA_SCHEDULE_AUTO = 0,
   GDA_SCHEDULE_PER_STEP = 1,
   GDA_SCHEDULE_RESIDENT = 2, /* GDA_ERR_UNSUPPORTED if not applicable */
-  GDA_SCHEDULE_PAIR = 3      /* per-step launches with two-SM tiles: clusters of
+  GDA_SCHEDULE_PAIR = 3,     /* per-step launches with two-SM tiles: clusters of
                               * two CTAs share 256 x BN tensor-core tiles
                               * (tcgen05 cta_group::2), each SM staging its 128
                               * rows of J and half of the operand columns;
@@ -171,6 +171,17 @@ typedef enum {
                               * multiple of 256, else GDA_ERR_UNSUPPORTED.
                               * AUTO uses them for per-step runs whose pair
                               * tiles fill three or more waves of clusters */
+  GDA_SCHEDULE_STREAM = 4    /* forward-Euler BF16 / FP8 steps of instances too
+                              * large for the resident kernel in one persistent
+                              * launch per tracking segment: the state streams
+                              * from HBM every step as with per-step launches,
+                              * but steps are ordered by per-tile flags, so the
+                              * next step's first tiles overlap the last
+                              * epilogues of the step before (two-SM tiles where
+                              * AUTO would take them); GDA_ERR_UNSUPPORTED for
+                              * RK4 or FP32 */,
+  GDA_SCHEDULE_STREAM_PAIR = 5 /* GDA_SCHEDULE_STREAM with two-SM tiles always
+                              * (conditions of GDA_SCHEDULE_PAIR) */
 } gda_schedule;
 
 /* Fills p with dt = 0.01, eps = 0.1, rho_th = 1, gamma0 = 0, beta0 = 1,

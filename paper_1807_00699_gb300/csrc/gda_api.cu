@@ -107,6 +107,8 @@ struct gda_ctx {
   int* d_zero = nullptr;
   int* err = nullptr;
   unsigned* flags = nullptr;  // per-tile step flags of the resident kernel
+  unsigned* seg_flags = nullptr;  // per-tile step flags of the persistent streaming kernel
+  size_t seg_flags_cap = 0;
   TcPlan* plan = nullptr;
   int cur = 0, bcur = 0, rcur = 0, opcur = 0;
   long long step = 0;
@@ -341,15 +343,18 @@ gda_status check_params(gda_ctx* c, const gda_params* p) {
   if (p->init_mode < 0 || p->init_mode > 3) return fail(c, GDA_ERR_INVALID, "init_mode must be 0, 1, 2 or 3");
   if (p->init_mode == 3 && !c->base) return fail(c, GDA_ERR_STATE, "init_mode 3 needs gda_set_init_base first");
   if (p->energy_every < 0) return fail(c, GDA_ERR_INVALID, "energy_every must be >= 0");
-  if (p->schedule < GDA_SCHEDULE_AUTO || p->schedule > GDA_SCHEDULE_PAIR)
+  if (p->schedule < GDA_SCHEDULE_AUTO || p->schedule > GDA_SCHEDULE_STREAM_PAIR)
     return fail(c, GDA_ERR_INVALID, "unknown schedule %d", p->schedule);
   if ((p->prec == GDA_BF16 || p->prec == GDA_FP8) && !c->tc_ok)
     return fail(c, GDA_ERR_UNSUPPORTED, "tensor-core path needs an sm_103 device");
   if (p->prec == GDA_SPARSE && p->schedule == GDA_SCHEDULE_RESIDENT)
     return fail(c, GDA_ERR_UNSUPPORTED, "the sparse product runs per step");
-  if (p->schedule == GDA_SCHEDULE_PAIR &&
+  if ((p->schedule == GDA_SCHEDULE_PAIR || p->schedule == GDA_SCHEDULE_STREAM_PAIR) &&
       (!(p->prec == GDA_BF16 || p->prec == GDA_FP8) || (c->Np / 128) % 2 != 0 || p->coupling != GDA_COUPLING_GD))
     return fail(c, GDA_ERR_UNSUPPORTED, "two-SM tiles need BF16 or FP8 and an even number of 128-row blocks");
+  if ((p->schedule == GDA_SCHEDULE_STREAM || p->schedule == GDA_SCHEDULE_STREAM_PAIR) &&
+      (!(p->prec == GDA_BF16 || p->prec == GDA_FP8) || p->integ != GDA_EULER || p->coupling != GDA_COUPLING_GD))
+    return fail(c, GDA_ERR_UNSUPPORTED, "the streaming schedule runs forward-Euler BF16 / FP8 steps");
   if (p->q != 0 && (p->q < 2 || p->q > 16)) return fail(c, GDA_ERR_INVALID, "q must be 0 or 2..16");
   if (!finite(p->wait_s) || p->wait_s < 0 || p->wait_s > 1e3)
     return fail(c, GDA_ERR_INVALID, "wait_s must be in [0, 1000] seconds");
@@ -542,6 +547,7 @@ void gda_destroy(gda_ctx* c) {
   dfree(c->bestE); dfree(c->bestR); dfree(c->cfg8); dfree(c->cfgth);
   dfree(c->E32); dfree(c->cidx); dfree(c->d_count); dfree(c->d_abs);
   dfree(c->t_step); dfree(c->t_E); dfree(c->t_r); dfree(c->t_count); dfree(c->err); dfree(c->flags);
+  dfree(c->seg_flags);
   dfree(c->lastE); dfree(c->lastR); dfree(c->snapE); dfree(c->snapR); dfree(c->snapStep); dfree(c->snap);
   dfree(c->hist);
   dfree(c->d_zero);
@@ -664,7 +670,7 @@ gda_status gda_run(gda_ctx* c, const gda_params* p, int32_t R, int64_t steps) {
   const bool tc = p->prec == GDA_BF16 || p->prec == GDA_FP8;
   const bool f8 = p->prec == GDA_FP8;
   c->run_sparse = false;
-  c->run_pair = p->schedule == GDA_SCHEDULE_PAIR;
+  c->run_pair = p->schedule == GDA_SCHEDULE_PAIR || p->schedule == GDA_SCHEDULE_STREAM_PAIR;
   c->potts_q = (c->cplx && p->q >= 2) ? p->q : 0;
   if (p->prec == GDA_SPARSE && p->coupling != GDA_COUPLING_GDMOD) {
     s = ensure_ell(c);
@@ -742,7 +748,60 @@ gda_status gda_run(gda_ctx* c, const gda_params* p, int32_t R, int64_t steps) {
                         (long long)((c->C + 127) / 128) * ((c->N + 127) / 128) <= kMaxResidentTiles;
   if (p->schedule == GDA_SCHEDULE_RESIDENT && !resident)
     return fail(c, GDA_ERR_UNSUPPORTED, "resident schedule needs BF16, Euler and a grid that fits the device");
-  if (tc && !resident && p->schedule == GDA_SCHEDULE_AUTO && tc_pair_pays(c->N, c->C)) c->run_pair = true;
+  if (tc && !resident && (p->schedule == GDA_SCHEDULE_AUTO || p->schedule == GDA_SCHEDULE_STREAM) &&
+      tc_pair_pays(c->N, c->C))
+    c->run_pair = true;
+  // persistent streaming launches: one per tracking segment, steps ordered by tile flags
+  if (tc && (p->schedule == GDA_SCHEDULE_STREAM || p->schedule == GDA_SCHEDULE_STREAM_PAIR)) {
+    const size_t nflags = size_t((c->C + 127) / 128) * size_t((c->N + 127) / 128);
+    if (c->seg_flags_cap < nflags) {
+      dfree(c->seg_flags);
+      c->seg_flags_cap = 0;
+      CK(dalloc(&c->seg_flags, nflags));
+      c->seg_flags_cap = nflags;
+    }
+    const int64_t seg = p->energy_every > 0 ? p->energy_every : steps;
+    for (int64_t k = 0; k < steps; k += seg) {
+      const int64_t len = std::min<int64_t>(seg, steps - k);
+      const int flip = int(len & 1);
+      StepArgs a = base;
+      a.mode = M_EULER;
+      a.step = static_cast<unsigned int>(c->step + k);
+      a.psi_n = c->psi[c->cur];
+      a.xs = c->psi[c->cur];
+      a.psi_out = c->psi[c->cur ^ 1];
+      a.beta_in = c->beta[c->bcur];
+      a.beta_out = c->beta[c->bcur ^ 1];
+      a.rho_in = c->rho[c->rcur];
+      a.rho_out = decay ? c->rho[c->rcur ^ 1] : nullptr;
+      SegArgs g{};
+      g.steps = int(len);
+      g.buf0 = c->opcur;
+      g.Cp = c->Cp;
+      g.flags = c->seg_flags;
+      g.psi[0] = c->psi[c->cur];
+      g.psi[1] = c->psi[c->cur ^ 1];
+      g.beta[0] = c->beta[c->bcur];
+      g.beta[1] = c->beta[c->bcur ^ 1];
+      g.rho[0] = c->rho[c->rcur];
+      g.rho[1] = c->rho[c->rcur ^ 1];
+      g.ops = f8 ? nullptr : c->ops;
+      g.ops8 = f8 ? c->ops8 : nullptr;
+      CK(cudaMemsetAsync(c->seg_flags, 0, nflags * sizeof(unsigned), c->stream));
+      LK(f8 ? launch_step_tcs8(c->plan8, a, g, c->stream, c->run_pair)
+            : launch_step_tcs(c->plan, a, g, c->stream, c->run_pair));
+      c->cur ^= flip;
+      c->bcur ^= flip;
+      c->opcur ^= flip;
+      if (decay) c->rcur ^= flip;
+      if (p->energy_every > 0 && len == seg) {
+        s = track(c, p, tc, c->step + k + len);
+        if (s != GDA_OK) return s;
+      }
+    }
+    c->step += steps;
+    return GDA_OK;
+  }
   if (resident) {
     const int64_t seg = p->energy_every > 0 ? p->energy_every : steps;
     for (int64_t k = 0; k < steps; k += seg) {

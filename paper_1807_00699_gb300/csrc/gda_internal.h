@@ -102,6 +102,20 @@ cudaError_t launch_prepare_ell(const float* J32, int N, int Np, int dmax, int* c
 // out[i][c] = x[c][i] for c < Cp, i < Np (column-major state -> spin-major operand).
 cudaError_t launch_transpose_state(const float* x, int Np, int Cp, float* out, cudaStream_t s);
 
+// One launch of the persistent multi-step tensor-core kernel (step_tcs.cuh):
+// forward-Euler steps whose buffers alternate with the step's parity.
+struct SegArgs {
+  int steps;                // steps of this launch
+  int buf0;                 // operand buffer holding the first step's operand
+  int Cp;                   // rows of one operand buffer
+  unsigned* flags;          // [column blocks][128-row blocks], zero at launch
+  float* psi[2];            // psi[0]: the first step's amplitudes; alternate per step
+  float* beta[2];           // likewise the coupling scales
+  float* rho[2];            // likewise the density partial sums (noise decay)
+  __nv_bfloat16* ops;       // BF16 operand buffers [2][Cp][Np] (or nullptr)
+  unsigned char* ops8;      // E4M3 operand buffers [2][Cp][Np] (FP8 path, or nullptr)
+};
+
 struct TcPlan;  // opaque plan holding the tensor maps of one context
 cudaError_t tc_plan_create(TcPlan** plan, const __nv_bfloat16* J16, int Np,
                            const __nv_bfloat16* ops, int n_op_bufs, int Cp);
@@ -114,6 +128,9 @@ cudaError_t launch_step_tc(const TcPlan* plan, const StepArgs& a, int op_buf, cu
 cudaError_t tc_plan8_create(TcPlan** plan, const unsigned char* J8, int Np, const unsigned char* ops8, int n_op_bufs,
                             int Cp);
 cudaError_t launch_step_tc8(const TcPlan* plan, const StepArgs& a, int op_buf, cudaStream_t s, bool pair = false);
+// g.steps forward-Euler steps in one persistent launch (BF16 / FP8 plans).
+cudaError_t launch_step_tcs(const TcPlan* plan, const StepArgs& a, const SegArgs& g, cudaStream_t s, bool pair);
+cudaError_t launch_step_tcs8(const TcPlan* plan, const StepArgs& a, const SegArgs& g, cudaStream_t s, bool pair);
 // q-state Potts projection (Sec. 1), in double: the q-th root of unity w_k = exp(2 pi i k / q)
 // maximising Re(conj(w_k) psi); ties and psi = 0 go to the lowest k.  In the
 // projection kernels the `cplx` argument is 0 (real spins), 1 (XY: psi / |psi|)

@@ -101,4 +101,8 @@ cudaError_t launch_step_tc(const TcPlan* plan, const StepArgs& a, int op_buf, cu
   return launch_plan<false>(plan, a, op_buf, pair, s);
 }
 
+cudaError_t launch_step_tcs(const TcPlan* plan, const StepArgs& a, const SegArgs& g, cudaStream_t s, bool pair) {
+  return launch_seg_plan<false>(plan, a, g, pair, s);
+}
+
 }  // namespace gda

@@ -491,3 +491,5 @@ cudaError_t launch_plan(const TcPlan* plan, const StepArgs& a, int op_buf, bool 
 }
 
 }  // namespace gda
+
+#include "step_tcs.cuh"

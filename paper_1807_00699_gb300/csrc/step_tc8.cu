@@ -69,6 +69,10 @@ cudaError_t tc_plan8_create(TcPlan** plan, const unsigned char* J8, int Np, cons
   return cudaSuccess;
 }
 
+cudaError_t launch_step_tcs8(const TcPlan* plan, const StepArgs& a, const SegArgs& g, cudaStream_t s, bool pair) {
+  return launch_seg_plan<true>(plan, a, g, pair, s);
+}
+
 cudaError_t launch_step_tc8(const TcPlan* plan, const StepArgs& a, int op_buf, cudaStream_t s, bool pair) {
   if (!a.row_scale) return cudaErrorInvalidValue;
   return launch_plan<true>(plan, a, op_buf, pair, s);

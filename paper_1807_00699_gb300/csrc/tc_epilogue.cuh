@@ -27,22 +27,11 @@ struct ModeTraits {
   static constexpr int l2_ahead = MODE == M_RAW ? 0 : 3;
 };
 
-// FP32 state is streamed once per step and is larger than L2: its loads and
-// stores carry an evict-first L2 policy, so that the coupling and operand
-// tiles the tensor cores re-read stay cached.
-static __device__ __forceinline__ uint64_t state_policy() {
-  uint64_t p;
-  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-  return p;
-}
-static __device__ __forceinline__ float ld_state(const float* p, uint64_t pol) {
-  float v;
-  asm volatile("ld.global.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
-  return v;
-}
-static __device__ __forceinline__ void st_state(float* p, float v, uint64_t pol) {
-  asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(v), "l"(pol));
-}
+// Loads and stores of the FP32 state.  (An evict-first L2 policy on them
+// measured slower: the lines the L2 prefetch brings in were dropped before
+// their loads.)
+static __device__ __forceinline__ float ld_state(const float* p) { return *p; }
+static __device__ __forceinline__ void st_state(float* p, float v) { *p = v; }
 
 template <int MODE, bool CPLX, int CW>
 struct EpiRegs {
@@ -67,17 +56,16 @@ __device__ __forceinline__ void epi_load(const StepArgs& a, int i, int c0, EpiRe
   constexpr int W = CPLX ? 2 : 1;
   const size_t Np = a.Np;
   const int r0 = CPLX ? c0 / 2 : c0;
-  const uint64_t pol = state_policy();
 #pragma unroll
   for (int k = 0; k < CW; ++k) {
     const size_t o = size_t(min(c0 + k, a.Cp - 1)) * Np + i;
     if (MODE == M_ENERGY) {
-      R.x[k] = ld_state(a.psi_n + o, pol);
+      R.x[k] = ld_state(a.psi_n + o);
     } else if (Tr::has_x) {
-      R.x[k] = ld_state(a.xs + o, pol);
+      R.x[k] = ld_state(a.xs + o);
       if (Tr::rk_mid) {
-        R.pn[k] = ld_state(a.psi_n + o, pol);
-        R.ac[k] = ld_state(a.acc + o, pol);
+        R.pn[k] = ld_state(a.psi_n + o);
+        R.ac[k] = ld_state(a.acc + o);
       }
     }
   }
@@ -85,10 +73,10 @@ __device__ __forceinline__ void epi_load(const StepArgs& a, int i, int c0, EpiRe
 #pragma unroll
     for (int u = 0; u < CW / W; ++u) {
       const size_t og = size_t(min(r0 + u, a.Rp - 1)) * Np + i;
-      R.gs[u] = ld_state(((MODE == M_EULER || MODE == M_RK1) ? a.gam : a.gstg) + og, pol);
+      R.gs[u] = ld_state(((MODE == M_EULER || MODE == M_RK1) ? a.gam : a.gstg) + og);
       if (Tr::rk_mid) {
-        R.gn[u] = ld_state(a.gam + og, pol);
-        R.ga[u] = ld_state(a.gacc + og, pol);
+        R.gn[u] = ld_state(a.gam + og);
+        R.ga[u] = ld_state(a.gacc + og);
       }
     }
   }
@@ -142,7 +130,6 @@ __device__ __forceinline__ void epi_chunk(const StepArgs& a, int i, int c0, cons
   const int r0 = CPLX ? c0 / 2 : c0;
   const bool row_ok = i < a.N;
   const float h = row_ok ? a.h1[i] : 0.0f;
-  const uint64_t pol = state_policy();
   const float gi = (MODE == M_ENERGY && row_ok) ? a.g[i] : 0.0f;
   float z[CW];
   if (MODE == M_EULER || MODE == M_RK4) {
@@ -213,18 +200,18 @@ __device__ __forceinline__ void epi_chunk(const StepArgs& a, int i, int c0, cons
       } else {
         const float cf = (MODE == M_RK3) ? a.dt : __fmul_rn(0.5f, a.dt);
         if (MODE == M_RK1) {
-          st_state(a.acc + o0, kr, pol);
-          if (CPLX) st_state(a.acc + o1, ki, pol);
-          st_state(a.gacc + og, kg, pol);
+          st_state(a.acc + o0, kr);
+          if (CPLX) st_state(a.acc + o1, ki);
+          st_state(a.gacc + og, kg);
         } else {
-          st_state(a.acc + o0, axpy(2.0f, kr, R.ac[ModeTraits<MODE>::rk_mid ? k0 : 0]), pol);
-          if (CPLX) st_state(a.acc + o1, axpy(2.0f, ki, R.ac[ModeTraits<MODE>::rk_mid ? k0 + 1 : 0]), pol);
-          st_state(a.gacc + og, axpy(2.0f, kg, R.ga[ModeTraits<MODE>::rk_mid ? u : 0]), pol);
+          st_state(a.acc + o0, axpy(2.0f, kr, R.ac[ModeTraits<MODE>::rk_mid ? k0 : 0]));
+          if (CPLX) st_state(a.acc + o1, axpy(2.0f, ki, R.ac[ModeTraits<MODE>::rk_mid ? k0 + 1 : 0]));
+          st_state(a.gacc + og, axpy(2.0f, kg, R.ga[ModeTraits<MODE>::rk_mid ? u : 0]));
         }
         const float sr = axpy(cf, kr, pr), si = axpy(cf, ki, pi);
-        st_state(a.xs_next + o0, sr, pol);
-        if (CPLX) st_state(a.xs_next + o1, si, pol);
-        st_state(a.gstg + og, axpy(cf, kg, gn), pol);
+        st_state(a.xs_next + o0, sr);
+        if (CPLX) st_state(a.xs_next + o1, si);
+        st_state(a.gstg + og, axpy(cf, kg, gn));
         if (a.op_out) {
           const size_t p0 = size_t(c0 + k0) * a.op_pitch + i;
           a.op_out[p0] = __float2bfloat16_rn(sr);
@@ -241,9 +228,9 @@ __device__ __forceinline__ void epi_chunk(const StepArgs& a, int i, int c0, cons
       nr = axpy(dsc[u], z[k0], nr);
       if (CPLX) ni = axpy(dsc[u], z[k0 + 1], ni);
     }
-    st_state(a.psi_out + o0, nr, pol);
-    if (CPLX) st_state(a.psi_out + o1, ni, pol);
-    st_state(a.gam + og, ng, pol);
+    st_state(a.psi_out + o0, nr);
+    if (CPLX) st_state(a.psi_out + o1, ni);
+    st_state(a.gam + og, ng);
     if (a.op_out) {
       const size_t p0 = size_t(c0 + k0) * a.op_pitch + i;
       a.op_out[p0] = __float2bfloat16_rn(nr);
