@@ -485,8 +485,9 @@ def run_ours(args):
     achieved = flops / t_kernel / 1e12
     resident = W["model"] == "xy" and prec == gda.BF16
     kname = ("step_res_kernel (resident: GEMM + fused epilogue, state in tensor memory), time per step" if resident
-             else {gda.BF16: "step_tc_kernel (per step, two-SM tiles at this size: GEMM + fused epilogue), time per step",
-                   gda.FP8: "step_tc_kernel (per step, E4M3 operands), time per step",
+             else {gda.BF16: "step_tcs_kernel (persistent streaming launch of all timed steps, two-SM tiles: GEMM + "
+                             "fused epilogue), time per step",
+                   gda.FP8: "step_tcs_kernel (persistent streaming launch, E4M3 operands), time per step",
                    gda.FP32: "step_simt_kernel"}[prec])
     traffic = TRAFFIC.get(args.workload) if prec == gda.BF16 else None
     roofline = {"bound": "alu" if prec == gda.FP32 else "tensor", "achieved": achieved, "peak": peak,

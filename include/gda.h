@@ -157,8 +157,10 @@ typedef enum { GDA_COUPLING_GD = 0, GDA_COUPLING_GDMOD = 1 } gda_coupling_mode;
 /* Launch schedule of the tensor-core path.  AUTO picks the resident kernel
  * for Euler runs whose 128 x 128 tiles all fit on the device at once (every
  * CTA keeps its tile's FP32 state in tensor memory for a whole segment of
- * steps, with a grid barrier between steps), else one launch per step (RK4
- * stage).  Both give the same numbers. */
+ * steps, with per-tile flags between steps); else, for Euler runs whose
+ * coupling operand (N'^2 BF16 or E4M3 values) fits in 48 MiB, the persistent
+ * streaming launch (GDA_SCHEDULE_STREAM); else one launch per step (RK4
+ * stage), with two-SM tiles where they pay.  All give the same numbers. */
 typedef enum {
   GDA_SCHEDULE_AUTO = 0,
   GDA_SCHEDULE_PER_STEP = 1,

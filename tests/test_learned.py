@@ -113,18 +113,28 @@ def test_short_training_reduces_loss(env):
     assert losses[-1] < 0.7 * losses[0]
 
 
-def test_trained_proposal_gain_over_plain(env):
-    # The committed network against the plain algorithm (default settings,
-    # small random start) on held-out seeds; FP64 energies decide.
+def test_trained_proposal_gain_over_best_fixed_setting(env):
+    """The committed network on held-out seeds (XY N = 1024, Ising N = 2048,
+    J ~ N(0, 1/N)) against plain GD at its default settings and at the best
+    fixed setting of the proposal's grid (calibrated per model on two other
+    seeds), BF16, R = 64, 5000 steps; an arm reaches the target when the
+    configuration its trace names is within 1e-3 of the best FP64 energy of
+    the three arms, in FP64.  The learned settings and start reach the target
+    on at least as many instances as either baseline, per model, and on more
+    instances than the best fixed setting overall."""
     torch, gda, lib = env
     from paper_1807_00699_gb300 import proposal
     prop = proposal.Proposal()
-    rows = proposal.evaluate(prop, [("ising", 2048, 10 ** 6 + 200), ("xy", 1024, 10 ** 6 + 201)], R=64, nsteps=1500,
-                             log=lambda *a: None)
-    ising, xy = rows
-    # Ising: the learned settings and start reach a lower energy than the plain run
-    assert ising["learned"]["E"] < ising["plain"]["E"] - 0.01 * abs(ising["plain"]["E"])
-    assert ising["learned"]["ttt_steps"] is not None
-    # XY: the gain is not significant (held-out evaluation: faster on 2 of 4
-    # seeds at 5000 steps, about equal mean energy); require no loss beyond 1 %
-    assert xy["learned"]["E"] <= xy["plain"]["E"] + 0.01 * abs(xy["plain"]["E"])
+    quiet = lambda *a: None  # noqa: E731
+    fixed = {"xy": proposal.best_fixed_setting("xy", 1024, [2 * 10 ** 6, 2 * 10 ** 6 + 1], log=quiet),
+             "ising": proposal.best_fixed_setting("ising", 2048, [2 * 10 ** 6 + 100, 2 * 10 ** 6 + 101], log=quiet)}
+    cases = [("xy", 1024, 10 ** 6 + k) for k in range(4)] + [("ising", 2048, 10 ** 6 + 100 + k) for k in range(4)]
+    rows = proposal.evaluate(prop, cases, fixed=fixed, log=quiet)
+    hits = {(m, arm): 0 for m in ("xy", "ising") for arm in ("plain", "best_fixed", "learned")}
+    for r in rows:
+        for arm in ("plain", "best_fixed", "learned"):
+            hits[(r["model"], arm)] += r[arm]["ttt_steps"] is not None
+    for m in ("xy", "ising"):
+        assert hits[(m, "learned")] >= hits[(m, "best_fixed")], hits
+        assert hits[(m, "learned")] >= hits[(m, "plain")], hits
+    assert sum(hits[(m, "learned")] for m in ("xy", "ising")) > sum(hits[(m, "best_fixed")] for m in ("xy", "ising"))
