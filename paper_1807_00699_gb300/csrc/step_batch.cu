@@ -596,7 +596,7 @@ struct gda_batch {
   float* base = nullptr;      // per-instance base amplitudes for init_mode 3 [sum N][2]
   int* err = nullptr;
   CUtensorMap tmA{}, tmB128{}, tmB256{};
-  BatchPlan plan[2];     // [width: 128, 256], units of both model types
+  BatchPlan plan[2][2];  // [persistent order, longest first][width: 128, 256], units of both model types
   int bn = 128;          // tile width in use (autotuned)
   bool persistent = true;  // one launch per chunk of steps (else one launch per step)
   std::vector<char> own;  // instance k has its own settings (gda_batch_set_params)
@@ -633,7 +633,11 @@ cudaError_t balloc(T** p, size_t n) {
 }
 
 // Longest-processing-time assignment of every instance's tiles to CTAs.
-gda_status build_plan(gda_batch* b, int bn, BatchPlan* P) {
+// sorted: within a CTA, units in one global order (instance, column block,
+// row block), so that a unit of the next step depends on tiles every CTA
+// finished early in this step (the persistent schedule); else longest first,
+// which leaves the short units for the end of a launch (one launch per step).
+gda_status build_plan(gda_batch* b, int bn, bool sorted, BatchPlan* P) {
   std::vector<BatchUnit> units;
   std::vector<double> cost;
   for (int k = 0; k < b->n; ++k) {
@@ -660,11 +664,9 @@ gda_status build_plan(gda_batch* b, int bn, BatchPlan* P) {
     bins[best].push_back(u);
     load[best] += cost[u];
   }
-  // within a CTA, units in one global order (instance, column block, row
-  // block): a unit of the next step then depends on tiles every CTA finished
-  // early in this step
   auto key = [&](int u) { return std::make_tuple(units[u].inst, units[u].nt, units[u].mt); };
-  for (auto& bin : bins) std::sort(bin.begin(), bin.end(), [&](int x, int y) { return key(x) < key(y); });
+  if (sorted)
+    for (auto& bin : bins) std::sort(bin.begin(), bin.end(), [&](int x, int y) { return key(x) < key(y); });
   std::vector<BatchUnit> flat;
   std::vector<int> begin(P->grid + 1, 0);
   for (int c = 0; c < P->grid; ++c) {
@@ -727,7 +729,7 @@ gda_status launch_chunk(gda_batch* b, const gda_params* p, unsigned off, int nst
   a.wait_cycles = p->wait_s > 0 ? (long long)(p->wait_s * kCyclesPerSecond) : kWaitCycles;
   a.err = b->err;
   const int wi = b->bn == 256 ? 1 : 0;
-  const BatchPlan& P = b->plan[wi];
+  const BatchPlan& P = b->plan[b->persistent ? 0 : 1][wi];
   if (P.n_units == 0) return GDA_OK;
   a.units = P.units;
   a.cta_begin = P.cta_begin;
@@ -912,10 +914,11 @@ gda_status gda_batch_create(int32_t n, const int32_t* N, const int32_t* model, c
     if (!encode(&b->tmA, b->J16, pitch, int(b->rowsJ), 128) || !encode(&b->tmB128, b->ops, pitch, int(b->rowsX), 128) ||
         !encode(&b->tmB256, b->ops, pitch, int(b->rowsX), 256))
       return bfail(b, GDA_ERR_CUDA, "tensor map encoding failed");
-    for (int wi = 0; wi < 2; ++wi) {
-      gda_status s = build_plan(b, wi ? 256 : 128, &b->plan[wi]);
-      if (s != GDA_OK) return s;
-    }
+    for (int oi = 0; oi < 2; ++oi)
+      for (int wi = 0; wi < 2; ++wi) {
+        gda_status s = build_plan(b, wi ? 256 : 128, oi == 0, &b->plan[oi][wi]);
+        if (s != GDA_OK) return s;
+      }
     BCK(set_batch_attrs());
     BCK(cudaDeviceSynchronize());
     return GDA_OK;
@@ -1126,10 +1129,11 @@ const char* gda_batch_last_error(const gda_batch* b) { return b ? b->msg.c_str()
 void gda_batch_destroy(gda_batch* b) {
   if (!b) return;
   if (b->graph) cudaGraphExecDestroy(b->graph);
-  for (auto& P : b->plan) {
-    if (P.units) cudaFree(P.units);
-    if (P.cta_begin) cudaFree(P.cta_begin);
-  }
+  for (auto& row : b->plan)
+    for (auto& P : row) {
+      if (P.units) cudaFree(P.units);
+      if (P.cta_begin) cudaFree(P.cta_begin);
+    }
   void* ptrs[] = {b->inst, b->J16, b->ops, b->J64, b->g64, b->off_J, b->off_g, b->psi, b->gam, b->h1, b->beta,
                   b->part, b->off_part, b->E_all, b->off_E, b->bestE, b->bestR, b->eunits, b->step_base, b->err,
                   b->flags, b->base};
