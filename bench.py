@@ -41,10 +41,10 @@ WORKLOADS = {
                    inst_seed=1),
 }
 METRIC = "time-to-target energy (s) & spin-updates/s: BF16+learned vs plain FP32 GDA"
-# DRAM bytes (read + write) per launch of each workload's dominant kernel, from
-# one-launch ncu captures (profiles/): None where no capture of the current
-# kernel exists.
-TRAFFIC = {"sk4096": None, "xy1000": None}
+# DRAM bytes (read + write) per step of each workload's dominant kernel, from
+# one-launch ncu captures (profiles/): the streaming kernel's 3-step launch moved
+# 873.3 + 482.1 MB; None where no capture of the current kernel exists.
+TRAFFIC = {"sk4096": (873.272064e6 + 482.108672e6) / 3, "xy1000": None}
 
 
 def parse():
@@ -491,7 +491,9 @@ def run_ours(args):
                    gda.FP32: "step_simt_kernel"}[prec])
     traffic = TRAFFIC.get(args.workload) if prec == gda.BF16 else None
     roofline = {"bound": "alu" if prec == gda.FP32 else "tensor", "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic, "kernel": kname,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+                "traffic_note": "DRAM bytes per step (one step = one unit of achieved), from a one-launch ncu "
+                                "capture of 3 steps scaled by steps" if traffic else None, "kernel": kname,
                 "peak_source": src, "us_per_launch": t_kernel * 1e6, "flop_per_launch": flops,
                 "launches_timed": nk}
 

@@ -10,6 +10,7 @@
 // order) are the dense kernel's, so density partials, noise decay and the
 // energy mode carry over unchanged.
 #include "epilogue.cuh"
+#include "tc_epilogue.cuh"
 
 namespace gda {
 namespace {
@@ -50,39 +51,47 @@ __global__ void __launch_bounds__(256) step_simt_kernel(StepArgs a, const float*
 
   float acc[4][4] = {};
   if (SPARSE) {
-    constexpr int KC = DW < 1 ? 1 : (DW < 8 ? DW : 8);  // entries whose loads are issued together
+    // The 4 rows' index loads, then their gathers, are issued together (rows
+    // beyond N read the ELL padding: column 0, value 0), so the dependent
+    // index -> gather chains of the rows overlap instead of following each other.
+    constexpr int KC = DW < 1 ? 1 : (DW < 4 ? DW : 4);  // entries per row whose loads are issued together
     const int cq = n0 + 4 * ty;          // the thread's 4 columns (always < Cp)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int i = m0 + tx + 16 * q;
-      if (i >= a.N) continue;
 #pragma unroll 1
-      for (int k0 = 0; k0 < DW; k0 += KC) {
-        int jj[KC];
-        float vv[KC];
+    for (int k0 = 0; k0 < DW; k0 += KC) {
+      int jj[4][KC];
+      float vv[4][KC];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
 #pragma unroll
         for (int k = 0; k < KC; ++k) {
-          const size_t o = size_t(k0 + k) * Np + i;
-          jj[k] = ell.col[o];
-          vv[k] = ell.val[o];
+          const size_t o = size_t(k0 + k) * Np + m0 + tx + 16 * q;
+          jj[q][k] = ell.col[o];
+          vv[q][k] = ell.val[o];
         }
-        if (a.opT_in) {  // spin-major operand: the 4 columns of spin j are one 16-byte load
-          float4 x[KC];
+      if (a.opT_in) {  // spin-major operand: the 4 columns of spin j are one 16-byte load
+        float4 x[4][KC];
 #pragma unroll
-          for (int k = 0; k < KC; ++k) x[k] = *reinterpret_cast<const float4*>(a.opT_in + size_t(jj[k]) * a.Cp + cq);
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+          for (int k = 0; k < KC; ++k)
+            x[q][k] = *reinterpret_cast<const float4*>(a.opT_in + size_t(jj[q][k]) * a.Cp + cq);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
 #pragma unroll
           for (int k = 0; k < KC; ++k) {
-            acc[q][0] = __fmaf_rn(vv[k], x[k].x, acc[q][0]);
-            acc[q][1] = __fmaf_rn(vv[k], x[k].y, acc[q][1]);
-            acc[q][2] = __fmaf_rn(vv[k], x[k].z, acc[q][2]);
-            acc[q][3] = __fmaf_rn(vv[k], x[k].w, acc[q][3]);
+            acc[q][0] = __fmaf_rn(vv[q][k], x[q][k].x, acc[q][0]);
+            acc[q][1] = __fmaf_rn(vv[q][k], x[q][k].y, acc[q][1]);
+            acc[q][2] = __fmaf_rn(vv[q][k], x[q][k].z, acc[q][2]);
+            acc[q][3] = __fmaf_rn(vv[q][k], x[q][k].w, acc[q][3]);
           }
-        } else {
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
 #pragma unroll
           for (int k = 0; k < KC; ++k)
 #pragma unroll
-            for (int u = 0; u < 4; ++u) acc[q][u] = __fmaf_rn(vv[k], X[size_t(cq + u) * Np + jj[k]], acc[q][u]);
-        }
+            for (int u = 0; u < 4; ++u)
+              acc[q][u] = __fmaf_rn(vv[q][k], X[size_t(cq + u) * Np + jj[q][k]], acc[q][u]);
       }
     }
   }
@@ -115,14 +124,34 @@ __global__ void __launch_bounds__(256) step_simt_kernel(StepArgs a, const float*
   const int lr0 = CPLX ? 2 * ty : 4 * ty;  // first local restart of the quad
   float rsum[4] = {0.f, 0.f, 0.f, 0.f};
   int bad = 0;
+  if (SPARSE) {
+    // every input of the 4 rows is loaded before the first store, so that the
+    // rows' loads are in flight together (the stores could alias them for the
+    // compiler); same arithmetic as epi_quad
+    EpiRegs<MODE, CPLX, 4> E[4];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int i = m0 + tx + 16 * q;
-    if (i >= a.N) continue;
-    float red[4];
-    epi_quad<CPLX, SPARSE, MODE>(a, i, c0, acc[q], &s_beta[lr0], &s_dsc[lr0], red, bad);
+    for (int q = 0; q < 4; ++q) epi_load<MODE, CPLX, 4>(a, m0 + tx + 16 * q, c0, E[q]);
 #pragma unroll
-    for (int u = 0; u < U; ++u) rsum[u] += red[u];
+    for (int q = 0; q < 4; ++q) {
+      const int i = m0 + tx + 16 * q;
+      if (i >= a.N) continue;
+      float red[4] = {0.f, 0.f, 0.f, 0.f}, t4[4];
+      epi_chunk<MODE, CPLX, 4, true>(a, i, c0, acc[q], E[q], &s_beta[lr0], &s_dsc[lr0], red, bad, t4);
+      if (a.opT_out && MODE != M_RAW && MODE != M_ENERGY)
+        *reinterpret_cast<float4*>(a.opT_out + size_t(i) * a.Cp + c0) = make_float4(t4[0], t4[1], t4[2], t4[3]);
+#pragma unroll
+      for (int u = 0; u < U; ++u) rsum[u] += red[u];
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int i = m0 + tx + 16 * q;
+      if (i >= a.N) continue;
+      float red[4];
+      epi_quad<CPLX, SPARSE, MODE>(a, i, c0, acc[q], &s_beta[lr0], &s_dsc[lr0], red, bad);
+#pragma unroll
+      for (int u = 0; u < U; ++u) rsum[u] += red[u];
+    }
   }
   // Sum over the 16 row groups (lanes with the same ty are one half-warp).
 #pragma unroll

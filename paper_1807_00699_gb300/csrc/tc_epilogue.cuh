@@ -119,11 +119,13 @@ __device__ __forceinline__ void epi_prefetch_l2(const StepArgs& a, int i, int c0
 // Arithmetic and stores of one chunk.  y: the CW accumulator values of row i.
 // beta_s / dsc: per-restart stage scale and noise amplitude, indexed by the
 // chunk's local restart.  red[u]: per-restart contribution (density of the
-// new amplitude, or Eq. (1) partial energy).
-template <int MODE, bool CPLX, int CW>
+// new amplitude, or Eq. (1) partial energy).  nxt (NXT only): receives the
+// chunk's next operand values (the new amplitudes, or the next RK stage
+// input), 0 for restarts beyond R.
+template <int MODE, bool CPLX, int CW, bool NXT = false>
 __device__ __forceinline__ void epi_chunk(const StepArgs& a, int i, int c0, const float* y,
                                           const EpiRegs<MODE, CPLX, CW>& R, const float* beta_s, const float* dsc,
-                                          float* red, int& bad) {
+                                          float* red, int& bad, float* nxt = nullptr) {
   constexpr int W = CPLX ? 2 : 1;
   constexpr int NR = CW / W;
   const size_t Np = a.Np;
@@ -148,6 +150,10 @@ __device__ __forceinline__ void epi_chunk(const StepArgs& a, int i, int c0, cons
 #pragma unroll
   for (int u = 0; u < NR; ++u) {
     red[u] = 0.0f;
+    if (NXT) {
+      nxt[u * W] = 0.0f;
+      if (CPLX) nxt[u * W + 1] = 0.0f;
+    }
     const int r = r0 + u;
     if (!row_ok || r >= a.R) continue;
     const int k0 = u * W;
@@ -209,6 +215,10 @@ __device__ __forceinline__ void epi_chunk(const StepArgs& a, int i, int c0, cons
           st_state(a.gacc + og, axpy(2.0f, kg, R.ga[ModeTraits<MODE>::rk_mid ? u : 0]));
         }
         const float sr = axpy(cf, kr, pr), si = axpy(cf, ki, pi);
+        if (NXT) {
+          nxt[k0] = sr;
+          if (CPLX) nxt[k0 + 1] = si;
+        }
         st_state(a.xs_next + o0, sr);
         if (CPLX) st_state(a.xs_next + o1, si);
         st_state(a.gstg + og, axpy(cf, kg, gn));
@@ -227,6 +237,10 @@ __device__ __forceinline__ void epi_chunk(const StepArgs& a, int i, int c0, cons
     if (MODE == M_EULER || MODE == M_RK4) {
       nr = axpy(dsc[u], z[k0], nr);
       if (CPLX) ni = axpy(dsc[u], z[k0 + 1], ni);
+    }
+    if (NXT) {
+      nxt[k0] = nr;
+      if (CPLX) nxt[k0 + 1] = ni;
     }
     st_state(a.psi_out + o0, nr);
     if (CPLX) st_state(a.psi_out + o1, ni);
