@@ -16,6 +16,7 @@ namespace gda {
 namespace {
 
 constexpr int BM = 64, BN = 64, BK = 16, PAD = 4;
+constexpr size_t kPairSmemMax = 200 * 1024;  // the staged sparse kernel: N rounded up to 128 <= 25600
 
 struct Ell {
   const int* col;   // [dmax][Np]
@@ -202,8 +203,143 @@ cudaError_t launch_step_simt(const StepArgs& a, const float* J32, const float* o
                 : launch_modes<false, false, 0>(a, J32, operand, none, s);
 }
 
+namespace {
+
+// Forward-Euler step over a sparse J0, one CTA per column pair (two Ising
+// restarts, or the real and imaginary columns of one XY restart): the pair's
+// amplitudes psi^n (two contiguous columns of Np floats) are staged in shared
+// memory once, then the CTA sweeps every row i, gathers sum_k val_ik X[col_ik]
+// from shared memory in ascending k (the per-step kernel's order, so Y has the
+// same bits) and runs the Euler update of Eqs. (2), (5), (6) on the staged
+// psi_i, with the same FP32 expression sequence as the other epilogues.  Each
+// amplitude is read from HBM once per step and no spin-major copy is kept.
+// Rows go to 16-thread groups by 64-row tile (thread tx of a group takes rows
+// tx + 16 q, q = 0..3), so the per-tile density sums are formed in the
+// per-step kernel's order and layout.
+constexpr int PAIR_THREADS = 512;
+
+template <bool CPLX, int DW>
+__global__ void __launch_bounds__(PAIR_THREADS) k_sparse_euler_pair(StepArgs a, Ell ell) {
+  extern __shared__ __align__(16) float xs[];  // [2][Np]: the pair's columns of psi^n
+  __shared__ float s_beta[2], s_dsc[2];
+  __shared__ int s_bad;
+  constexpr int U = CPLX ? 1 : 2;  // restarts of the pair
+  const int tid = threadIdx.x;
+  const int Np = a.Np;
+  const int c0 = 2 * blockIdx.x;           // first column of the pair (< Cp)
+  const int r0 = CPLX ? blockIdx.x : c0;   // first restart
+  // stage psi^n of both columns (coalesced 16-byte loads)
+  {
+    const float4* src0 = reinterpret_cast<const float4*>(a.psi_n + size_t(c0) * Np);
+    const float4* src1 = reinterpret_cast<const float4*>(a.psi_n + size_t(c0 + 1) * Np);
+    float4* dst = reinterpret_cast<float4*>(xs);
+    const int n4 = Np / 4;
+    for (int k = tid; k < n4; k += PAIR_THREADS) {
+      dst[k] = src0[k];
+      dst[n4 + k] = src1[k];
+    }
+  }
+  if (tid == 0) s_bad = 0;
+  if (tid < U) {
+    const int r = r0 + tid;
+    const float b = r < a.R ? a.beta_in[r] : 1.0f;
+    s_beta[tid] = stage_beta(a, b);
+    s_dsc[tid] = r < a.R ? noise_scale(a, r) : 0.0f;
+  }
+  __syncthreads();
+  const float* x0 = xs;
+  const float* x1 = xs + Np;
+  const bool noise = s_dsc[0] != 0.0f || (U > 1 && s_dsc[1] != 0.0f);
+  int bad = 0;
+  const int grp = tid >> 4, tx = tid & 15;
+  // the two halves of a warp may run different numbers of tiles: shuffles
+  // stay within the half
+  const unsigned half = (tid & 16) ? 0xffff0000u : 0x0000ffffu;
+  for (int t = grp; t < a.mt_count; t += PAIR_THREADS / 16) {  // 64-row tiles
+   float red[2] = {0.0f, 0.0f};
+#pragma unroll
+   for (int qq = 0; qq < 4; ++qq) {
+    const int i = t * 64 + tx + 16 * qq;
+    if (i >= a.N) continue;
+    float y0 = 0.0f, y1 = 0.0f;
+#pragma unroll
+    for (int k = 0; k < DW; ++k) {
+      const size_t o = size_t(k) * Np + i;
+      const int j = ell.col[o];
+      const float v = ell.val[o];
+      y0 = __fmaf_rn(v, x0[j], y0);
+      y1 = __fmaf_rn(v, x1[j], y1);
+    }
+    float z[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    if (noise) philox_normal4(uint32_t(i), uint32_t(c0 >> 2), a.step, 0u, a.seed, z);
+    const float h = a.h1[i];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int r = r0 + u;
+      if (r >= a.R) continue;
+      const int col = c0 + u;  // Ising: the restart's column; XY: the real part's
+      const size_t og = size_t(r) * Np + i;
+      const float xr = u == 0 ? x0[i] : x1[i];
+      const float xi = CPLX ? x1[i] : 0.0f;
+      const float yr = u == 0 ? y0 : y1;
+      const float yi = CPLX ? y1 : 0.0f;
+      const float gs = a.gam[og];
+      float kr, ki, kg;
+      gd_rhs(xr, xi, gs, yr, yi, s_beta[u], h, a.eps, a.rho_th, kr, ki, kg);
+      if (CPLX && a.q) resonant_drive(xr, xi, a.q, a.hq, kr, ki);
+      float nr = axpy(a.dt, kr, xr);
+      float ni = axpy(a.dt, ki, xi);
+      const float ng = axpy(a.dt, kg, gs);
+      nr = axpy(s_dsc[u], z[col & 3], nr);
+      if (CPLX) ni = axpy(s_dsc[u], z[(col + 1) & 3], ni);
+      a.psi_out[size_t(col) * Np + i] = nr;
+      if (CPLX) a.psi_out[size_t(col + 1) * Np + i] = ni;
+      a.gam[og] = ng;
+      const float rn = density(nr, ni);
+      red[u] += rn;
+      bad |= !(rn < 1e30f);
+    }
+   }
+   if (a.rho_out) {  // the tile's density sum per restart: an xor tree over the group's 16 threads
+#pragma unroll
+     for (int u = 0; u < U; ++u) {
+       float v = red[u];
+#pragma unroll
+       for (int off = 8; off; off >>= 1) v += __shfl_xor_sync(half, v, off);
+       if (tx == 0 && r0 + u < a.R) a.rho_out[size_t(t) * a.Rp + r0 + u] = v;
+     }
+   }
+  }
+  if (bad) atomicOr(&s_bad, 1);
+  __syncthreads();
+  if (tid < U) {
+    const int r = r0 + tid;
+    if (r < a.R) a.beta_out[r] = next_beta(a, a.beta_in[r]);
+  }
+  if (tid == 0 && s_bad) atomicOr(a.err, E_DIVERGED);
+}
+
+template <bool CPLX, int DW>
+cudaError_t launch_pair(const StepArgs& a, const Ell& ell, cudaStream_t s) {
+  const size_t smem = size_t(2) * a.Np * sizeof(float);
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_sparse_euler_pair<CPLX, DW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kPairSmemMax);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k_sparse_euler_pair<CPLX, DW><<<(a.C + 1) / 2, PAIR_THREADS, smem, s>>>(a, ell);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
 template <int DW>
 cudaError_t launch_sparse_w(const StepArgs& a, const Ell& ell, const float* operand, cudaStream_t s) {
+  // Euler steps whose column pair fits in shared memory: the staged kernel
+  if (a.mode == M_EULER && size_t(2) * a.Np * sizeof(float) <= kPairSmemMax)
+    return a.cplx ? launch_pair<true, DW>(a, ell, s) : launch_pair<false, DW>(a, ell, s);
   return a.cplx ? launch_modes<true, true, DW>(a, nullptr, operand, ell, s)
                 : launch_modes<false, true, DW>(a, nullptr, operand, ell, s);
 }

@@ -367,3 +367,27 @@ def test_init_mode_3_base_plus_perturbation_bit_exact(gda, model):
         ref = (base.astype(np.float32) + pert.astype(np.float32)).astype(np.float64)
     assert np.array_equal(psi.astype(ref.dtype), ref)
     s.close()
+
+
+def test_headline_xy_schedule_300_steps(gda):
+    """The XY N = 1000, R = 1024 workload's exact parameters (dt = 0.05,
+    eps = 0.1, tracking every 100 steps, seeded 1e-3 start) for 300 steps:
+    the resident kernel equals per-step launches bit for bit (state and trace),
+    and the FP64 energies of the returned spins equal the oracle's Eq. (1)."""
+    n, R = 1000, 1024
+    J, g = synth.xy_gaussian(n, 1)
+    kw = dict(dt=0.05, eps=0.1, rho_th=1.0, init_mode=1, init_amp=1e-3, seed=1, energy_every=100, prec=gda.BF16)
+    out = {}
+    for sched in (gda.RESIDENT, gda.PER_STEP):
+        s = gda.Solver(J, g, gda.XY)
+        s.run(gda.default_params(schedule=sched, **kw), R, 300)
+        psi = s.get_state()[0]
+        out[sched] = (psi, s.trace(), s.energy(), s.trace_energy())
+        s.close()
+    a, b = out[gda.RESIDENT], out[gda.PER_STEP]
+    assert np.array_equal(a[0], b[0])
+    for x, y in zip(a[1], b[1]):
+        assert np.array_equal(x, y)
+    assert np.array_equal(a[2], b[2]) and np.array_equal(a[3], b[3])
+    ref = oracle.energies(J, g, oracle.project(a[0].astype(np.complex128)))
+    assert np.allclose(a[2], ref, rtol=1e-9, atol=0)
