@@ -216,9 +216,9 @@ namespace {
 // Rows go to 16-thread groups by 64-row tile (thread tx of a group takes rows
 // tx + 16 q, q = 0..3), so the per-tile density sums are formed in the
 // per-step kernel's order and layout.
-constexpr int PAIR_THREADS = 512;
-
-template <bool CPLX, int DW>
+// PAIR_THREADS threads per CTA: 512 where two CTAs share an SM, 1024 where the
+// staged columns take most of an SM's shared memory (more loads in flight).
+template <bool CPLX, int DW, int PAIR_THREADS>
 __global__ void __launch_bounds__(PAIR_THREADS) k_sparse_euler_pair(StepArgs a, Ell ell) {
   extern __shared__ __align__(16) float xs[];  // [2][Np]: the pair's columns of psi^n
   __shared__ float s_beta[2], s_dsc[2];
@@ -319,18 +319,24 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_sparse_euler_pair(StepArgs a, 
   if (tid == 0 && s_bad) atomicOr(a.err, E_DIVERGED);
 }
 
-template <bool CPLX, int DW>
-cudaError_t launch_pair(const StepArgs& a, const Ell& ell, cudaStream_t s) {
-  const size_t smem = size_t(2) * a.Np * sizeof(float);
+template <bool CPLX, int DW, int NT>
+cudaError_t launch_pair_nt(const StepArgs& a, const Ell& ell, size_t smem, cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_sparse_euler_pair<CPLX, DW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kPairSmemMax);
+    cudaError_t e = cudaFuncSetAttribute(k_sparse_euler_pair<CPLX, DW, NT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kPairSmemMax);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  k_sparse_euler_pair<CPLX, DW><<<(a.C + 1) / 2, PAIR_THREADS, smem, s>>>(a, ell);
+  k_sparse_euler_pair<CPLX, DW, NT><<<(a.C + 1) / 2, NT, smem, s>>>(a, ell);
   return cudaGetLastError();
+}
+
+template <bool CPLX, int DW>
+cudaError_t launch_pair(const StepArgs& a, const Ell& ell, cudaStream_t s) {
+  const size_t smem = size_t(2) * a.Np * sizeof(float);
+  return smem <= size_t(110) * 1024 ? launch_pair_nt<CPLX, DW, 512>(a, ell, smem, s)
+                                    : launch_pair_nt<CPLX, DW, 1024>(a, ell, smem, s);
 }
 
 }  // namespace
