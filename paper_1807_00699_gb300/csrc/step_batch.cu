@@ -137,10 +137,9 @@ __device__ __forceinline__ bool epi_unit(const BatchArgs& b, const BatchInst& I,
                                          float* s_beta, float* s_dsc, int* s_flag, StepArgs* s_args, int& bad) {
   constexpr int W = CPLX ? 2 : 1;
   constexpr int RPT = BN / W;
-  constexpr int NPART = NEPI / 4;      // column parts
-  constexpr int PW = BN / NPART;       // columns per part
+  constexpr int PW = BN / (NEPI / 4);  // columns per part
   constexpr int CW = 8;
-  constexpr int NCH = PW / CW;         // chunks per part
+  constexpr int NCH = PW / CW;
   static_assert(PW % CW == 0, "column part must hold whole chunks");
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int e = threadIdx.x - 64;
@@ -155,19 +154,13 @@ __device__ __forceinline__ bool epi_unit(const BatchArgs& b, const BatchInst& I,
   const int m0 = U.mt * BM, n0 = U.nt * BN;
   const int rbase = n0 / W;
   const int i = m0 + 32 * q + lane;
+  const int cbeg = n0 + part * PW;
   const unsigned* fl = b.flags + I.flag0 + U.nt * I.mt;
-  // chunks go to the column parts in turn (chunk g = part + NPART k, columns
-  // n0 + g CW ..), and only the chunks holding one of the instance's columns
-  // are processed, by the warps whose row quarter holds one of its spins: a
-  // small instance in a 128 x BN tile costs in proportion to its size
-  const int ncols = min(BN, I.C - n0);
-  const int nvc = (ncols + CW - 1) / CW;  // chunks holding a column
-  const int nact = (m0 + 32 * q < I.N && nvc > part) ? min(NCH, (nvc - part + NPART - 1) / NPART) : 0;
-  auto col0 = [&](int k) { return n0 + (part + NPART * k) * CW; };
   constexpr int PF = ModeTraits<M_EULER>::l2_ahead;  // chunks pulled into L2 ahead of their loads
-  for (int k = 1; k <= PF && k < nact; ++k) epi_prefetch_l2<M_EULER, CPLX, CW>(a, i, col0(k), lane);
+#pragma unroll
+  for (int p = 1; p <= PF && p < NCH; ++p) epi_prefetch_l2<M_EULER, CPLX, CW>(a, i, cbeg + p * CW, lane);
   EpiRegs<M_EULER, CPLX, CW> R[2];
-  if (nact > 0) epi_load<M_EULER, CPLX, CW>(a, i, col0(0), R[0]);  // own rows of psi and gamma: written by this thread
+  epi_load<M_EULER, CPLX, CW>(a, i, cbeg, R[0]);  // own rows of psi and gamma: written by this thread
   bool fok = true;
   if (e < RPT) {
     // beta^n of this column block was written by unit (k, 0, n) at the previous step
@@ -185,21 +178,22 @@ __device__ __forceinline__ bool epi_unit(const BatchArgs& b, const BatchInst& I,
     atomicOr(&s_flag[0], 1);
     return false;
   }
-  const uint32_t taddr = tacc + (static_cast<uint32_t>(32 * q) << 16);
-  auto body = [&](int k, const EpiRegs<M_EULER, CPLX, CW>& cr, EpiRegs<M_EULER, CPLX, CW>& nx) {
-    if (k + 1 + PF < nact) epi_prefetch_l2<M_EULER, CPLX, CW>(a, i, col0(k + 1 + PF), lane);
-    if (k + 1 < nact) epi_load<M_EULER, CPLX, CW>(a, i, col0(k + 1), nx);
-    const int lc = col0(k) - n0;  // the chunk's first local column
+  const uint32_t taddr = tacc + (static_cast<uint32_t>(32 * q) << 16) + part * PW;
+  auto body = [&](int ch, const EpiRegs<M_EULER, CPLX, CW>& cr, EpiRegs<M_EULER, CPLX, CW>& nx) {
+    if (ch + 1 + PF < NCH) epi_prefetch_l2<M_EULER, CPLX, CW>(a, i, cbeg + (ch + 1 + PF) * CW, lane);
+    if (ch + 1 < NCH) epi_load<M_EULER, CPLX, CW>(a, i, cbeg + (ch + 1) * CW, nx);
     float v[CW];
-    tmem_ld<CW>(taddr + lc, v);
+    tmem_ld<CW>(taddr + ch * CW, v);
+    const int lr0 = (part * PW + ch * CW) / W;
     float red[CW / W];
-    epi_chunk<M_EULER, CPLX, CW>(a, i, col0(k), v, cr, &s_beta[lc / W], &s_dsc[lc / W], red, bad);
+    epi_chunk<M_EULER, CPLX, CW>(a, i, cbeg + ch * CW, v, cr, &s_beta[lr0], &s_dsc[lr0], red, bad);
   };
 #pragma unroll 1
-  for (int k = 0; k < nact; k += 2) {  // warp-uniform bounds: tcgen05.ld is warp-collective
-    body(k, R[0], R[1]);
-    if (k + 1 < nact) body(k + 1, R[1], R[0]);
+  for (int ch = 0; ch + 1 < NCH; ch += 2) {
+    body(ch, R[0], R[1]);
+    body(ch + 1, R[1], R[0]);
   }
+  if (NCH & 1) body(NCH - 1, R[0], R[1]);
   const bool publish = b.nsteps > 1;  // later steps of this launch read what this unit wrote
   tc_fence_before();
   if (publish) fence_proxy_async_global();  // the next operand rows are read by other CTAs' TMA loads
