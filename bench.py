@@ -385,7 +385,9 @@ def batched_learned_arm(gda, torch, stream, prop, solver, J, g, W, R, k_hit, t_p
     row = {"ttt_s": t_prop + t_batch * share, "steps_to_target": k_hit, "batch_s_to_step": t_batch,
            "instances": len(insts), "flop_share": share, "settings": settings, "proposal_s": t_prop,
            "bit_identical_to_single_run": same, "launch_mode": "graph" if bt.launch_mode() == 1 else "direct",
-           "batch_spin_updates_per_s": sum(Jk.shape[0] * Rk for Jk, _, _, Rk in insts) * k_hit / t_batch}
+           "batch_spin_updates_per_s": sum(Jk.shape[0] * Rk for Jk, _, _, Rk in insts) * k_hit / t_batch,
+           # the batch's coupling products (2 N^2 C per instance and step) against its run time
+           "batch_tflops": sum(flops) * k_hit / t_batch / 1e12}
     bt.close()
     return row
 
