@@ -182,19 +182,27 @@ def _features_dev(J, g, xy):
     return F
 
 
-def train(n_inst=384, epochs=40, batch=16, lr=2e-3, wset=0.5, seed=0, log=print):
+def train(n_inst=384, epochs=40, batch=16, lr=2e-3, wset=0.5, seed=0, log=print, target_minutes=None):
     """Generates targets with plain GD runs and trains the network with the
-    library's kernels (forward, loss, backward, Adam); returns (params, losses)."""
+    library's kernels (forward, loss, backward, Adam); returns (params, losses).
+    target_minutes: a wall-clock budget for the target runs; the instances
+    generated within it are used (log reports how many)."""
+    import time
     import torch
     lib = gda.load_library()
     data = []
+    t0 = time.time()
     for k in range(n_inst):
         J, g, xy = training_instance(k)
         S, setting = make_targets(J, g, xy, seed=k + 1)
         data.append((_features_dev(J, g, xy), torch.tensor(S, dtype=torch.float32, device="cuda"),
                      outputs_from_settings(*setting), xy))
-        if (k + 1) % 64 == 0:
-            log(f"targets {k + 1}/{n_inst}")
+        if (k + 1) % 256 == 0:
+            log(f"targets {k + 1}/{n_inst} in {time.time() - t0:.0f} s")
+        if target_minutes is not None and time.time() - t0 > 60.0 * target_minutes:
+            log(f"target budget reached after {k + 1} instances")
+            break
+    n_inst = len(data)
     p = torch.tensor(init_params(seed), device="cuda")
     m1 = torch.zeros_like(p)
     m2 = torch.zeros_like(p)
@@ -340,13 +348,16 @@ def main(argv=None):
     ap.add_argument("--epochs", type=int, default=40)
     ap.add_argument("--out", default=PARAMS_PATH)
     ap.add_argument("--report", default=None)
+    ap.add_argument("--target-minutes", type=float, default=None)
     a = ap.parse_args(argv)
     torch.cuda.set_device(0)
     if a.cmd == "train":
-        params, losses = train(n_inst=a.n_inst, epochs=a.epochs)
+        used = []
+        params, losses = train(n_inst=a.n_inst, epochs=a.epochs, target_minutes=a.target_minutes,
+                               log=lambda m: (print(m, flush=True), used.append(m)))
         os.makedirs(os.path.dirname(a.out), exist_ok=True)
         np.save(a.out, params)
-        report = {"losses": losses}
+        report = {"losses": losses, "log": used}
     else:
         prop = Proposal(np.load(a.out))
         fixed = {"xy": best_fixed_setting("xy", 1024, [2 * 10 ** 6, 2 * 10 ** 6 + 1]),
