@@ -401,7 +401,7 @@ gda_status gda_adam_step(float* params, const float* grad, float* m1, float* m2,
  * every instance (both model types) over all their 128 x BN output tiles,
  * with steps ordered by per-tile dataflow flags (or, by choice, one launch per
  * step: gda_batch_set_schedule); chunks replay from a captured CUDA graph
- * where the driver captures the launch (gda_batch_launch_mode).
+ * where the CUDA runtime captures the launch (gda_batch_launch_mode).
  * Every instance follows exactly the single-instance forward-Euler BF16
  * dynamics (Eqs. 2, 5, 6) with its own Philox seed and, optionally, its own
  * settings and start (gda_batch_set_params, gda_batch_set_init_base).  The
@@ -451,7 +451,7 @@ gda_status gda_batch_set_params(gda_batch* b, int32_t k, const gda_params* p);
 gda_status gda_batch_set_init_base(gda_batch* b, int32_t k, const float* base, int32_t on_device);
 
 /* 1 if the batch's chunks replay a captured CUDA graph, 0 if they are
- * launched directly (the driver declined to capture the cooperative launch),
+ * launched directly (the CUDA runtime declined to capture the cooperative launch),
  * -1 for b = NULL. */
 int32_t gda_batch_launch_mode(const gda_batch* b);
 

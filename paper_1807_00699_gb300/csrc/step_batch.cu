@@ -1045,7 +1045,7 @@ gda_status gda_batch_run(gda_batch* b, const gda_params* p, int64_t steps) {
     cudaError_t ie = cudaErrorUnknown;
     if (s == GDA_OK && ce == cudaSuccess) ie = cudaGraphInstantiate(&b->graph, g, 0);
     if (g) cudaGraphDestroy(g);
-    if (ie != cudaSuccess) {  // the driver does not capture this launch: chunks launch directly
+    if (ie != cudaSuccess) {  // the CUDA runtime declined to capture this launch: chunks launch directly
       cudaGetLastError();
       b->graph = nullptr;
       b->graph_failed = true;
