@@ -600,6 +600,16 @@ def run_batched(args):
     t = float(np.mean(times))
     upd = sum(d["n"] * d["r"] for d in descs) * steps
     flops = sum(2.0 * d["n"] ** 2 * d["r"] * (2 if d["model"] == "xy" else 1) for d in descs) * steps
+    # the mix's BF16 couplings (2.1 GB at 2000 instances) do not fit in L2, so a
+    # step streams them and the FP32 state from HBM: algorithmic bytes per step
+    # = J once (2 N^2) + psi read and written (8 N C) + gamma read and written
+    # (8 N R) + the BF16 operand written and read once (4 N C)
+    def step_bytes(d):
+        n, r = d["n"], d["r"]
+        c = r * (2 if d["model"] == "xy" else 1)
+        return 2.0 * n * n + 8.0 * n * c + 8.0 * n * r + 4.0 * n * c
+    hbm_bytes = sum(step_bytes(d) for d in descs)
+    hbm_peak = load_peaks().get("hbm_gbs")
     # unbatched comparison: the first 50 instances one by one through the single-instance API
     sub = insts[:50]
     e0 = torch.cuda.Event(enable_timing=True)
@@ -624,6 +634,9 @@ def run_batched(args):
                        "tile_bn": bn, "schedule": sched, "tune_s_per_step": tune, "setup_s": setup_s,
                        "l2": "flushed (256 MB write) between timed steps"},
             "tflops": flops / t / 1e12, "clocks": clocks.summary(),
+            "hbm": {"bytes_per_step": hbm_bytes, "gbs": hbm_bytes * steps / t / 1e9, "peak_gbs": hbm_peak,
+                    "frac": (hbm_bytes * steps / t / 1e9 / hbm_peak) if hbm_peak else None,
+                    "peak_note": "of measured (MEASURED_PEAKS.json hbm_gbs)"},
             "unbatched_first50": {"spin_updates_per_s": upd_sub / t_sub, "s": t_sub},
             "batched_first50_equivalent": upd_sub / (upd / t)}
     print(json.dumps(line), flush=True)

@@ -11,6 +11,7 @@
 // energy mode carry over unchanged.
 #include "epilogue.cuh"
 #include "tc_epilogue.cuh"
+#include "tc_ptx.cuh"
 
 namespace gda {
 namespace {
@@ -208,7 +209,7 @@ namespace {
 // Forward-Euler step over a sparse J0, one CTA per column pair (two Ising
 // restarts, or the real and imaginary columns of one XY restart): the pair's
 // amplitudes psi^n (two contiguous columns of Np floats) are staged in shared
-// memory once, then the CTA sweeps every row i, gathers sum_k val_ik X[col_ik]
+// memory once (bulk asynchronous copies), then the CTA sweeps every row i, gathers sum_k val_ik X[col_ik]
 // from shared memory in ascending k (the per-step kernel's order, so Y has the
 // same bits) and runs the Euler update of Eqs. (2), (5), (6) on the staged
 // psi_i, with the same FP32 expression sequence as the other epilogues.  Each
@@ -223,21 +224,26 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_sparse_euler_pair(StepArgs a, 
   extern __shared__ __align__(16) float xs[];  // [2][Np]: the pair's columns of psi^n
   __shared__ float s_beta[2], s_dsc[2];
   __shared__ int s_bad;
+  __shared__ __align__(8) uint64_t s_bar;
   constexpr int U = CPLX ? 1 : 2;  // restarts of the pair
   const int tid = threadIdx.x;
   const int Np = a.Np;
   const int c0 = 2 * blockIdx.x;           // first column of the pair (< Cp)
   const int r0 = CPLX ? blockIdx.x : c0;   // first restart
-  // stage psi^n of both columns (coalesced 16-byte loads)
-  {
-    const float4* src0 = reinterpret_cast<const float4*>(a.psi_n + size_t(c0) * Np);
-    const float4* src1 = reinterpret_cast<const float4*>(a.psi_n + size_t(c0 + 1) * Np);
-    float4* dst = reinterpret_cast<float4*>(xs);
-    const int n4 = Np / 4;
-    for (int k = tid; k < n4; k += PAIR_THREADS) {
-      dst[k] = src0[k];
-      dst[n4 + k] = src1[k];
-    }
+  // stage psi^n of both columns: bulk copies of <= 32 KB (Np is a multiple
+  // of 128, so every piece is a multiple of 16 bytes and 16-byte aligned)
+  const uint32_t bar = ptx::smem_u32(&s_bar);
+  if (tid == 0) {
+    ptx::mbar_init(bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    const uint32_t col_bytes = uint32_t(Np) * 4u;
+    ptx::mbar_arrive_expect_tx(bar, 2u * col_bytes);
+    for (int u = 0; u < 2; ++u)
+      for (uint32_t off = 0; off < col_bytes; off += 32768u) {
+        const uint32_t len = col_bytes - off < 32768u ? col_bytes - off : 32768u;
+        ptx::bulk_load(ptx::smem_u32(xs) + uint32_t(u) * col_bytes + off,
+                       reinterpret_cast<const char*>(a.psi_n + size_t(c0 + u) * Np) + off, len, bar);
+      }
   }
   if (tid == 0) s_bad = 0;
   if (tid < U) {
@@ -246,7 +252,14 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_sparse_euler_pair(StepArgs a, 
     s_beta[tid] = stage_beta(a, b);
     s_dsc[tid] = r < a.R ? noise_scale(a, r) : 0.0f;
   }
-  __syncthreads();
+  __syncthreads();  // publishes the barrier's initialisation and s_beta / s_dsc
+  // every thread waits for the copies (bounded); a CTA whose copies did not
+  // land in time reports a timeout and leaves once they have (again bounded)
+  if (!__syncthreads_and(ptx::mbar_wait(bar, 0, a.wait_cycles))) {
+    if (tid == 0) atomicOr(a.err, E_TIMEOUT);
+    (void)ptx::mbar_wait(bar, 0, a.wait_cycles);
+    return;
+  }
   const float* x0 = xs;
   const float* x1 = xs + Np;
   const bool noise = s_dsc[0] != 0.0f || (U > 1 && s_dsc[1] != 0.0f);
@@ -256,23 +269,46 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_sparse_euler_pair(StepArgs a, 
   // stay within the half
   const unsigned half = (tid & 16) ? 0xffff0000u : 0x0000ffffu;
   for (int t = grp; t < a.mt_count; t += PAIR_THREADS / 16) {  // 64-row tiles
-   float red[2] = {0.0f, 0.0f};
+   // the tile's four rows of a thread: every load first (the gathers, the
+   // gains, the fields), then the updates and stores, so that no store sits
+   // between two loads and a thread keeps all of them in flight
+   float y[4][2], gv[4][U], hv[4];
+   {  // the next tile's gain lines (two 128-byte lines per restart) into L2
+     const int tn = t + PAIR_THREADS / 16;
+     if (tn < a.mt_count && tx < 2 * U && r0 + (tx >> 1) < a.R)
+       prefetch_l2(a.gam + size_t(r0 + (tx >> 1)) * Np + tn * 64 + 32 * (tx & 1));
+   }
 #pragma unroll
    for (int qq = 0; qq < 4; ++qq) {
     const int i = t * 64 + tx + 16 * qq;
-    if (i >= a.N) continue;
+    const bool ok = i < a.N;
+    const int ic = ok ? i : 0;
     float y0 = 0.0f, y1 = 0.0f;
 #pragma unroll
     for (int k = 0; k < DW; ++k) {
-      const size_t o = size_t(k) * Np + i;
+      const size_t o = size_t(k) * Np + ic;
       const int j = ell.col[o];
       const float v = ell.val[o];
       y0 = __fmaf_rn(v, x0[j], y0);
       y1 = __fmaf_rn(v, x1[j], y1);
     }
+    y[qq][0] = y0;
+    y[qq][1] = y1;
+    hv[qq] = a.h1[ic];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      gv[qq][u] = ok && r0 + u < a.R ? a.gam[size_t(r0 + u) * Np + i] : 0.0f;
+   }
+   float red[2] = {0.0f, 0.0f};
+#pragma unroll
+   for (int qq = 0; qq < 4; ++qq) {
+    const int i = t * 64 + tx + 16 * qq;
+    if (i >= a.N) continue;
     float z[4] = {0.0f, 0.0f, 0.0f, 0.0f};
     if (noise) philox_normal4(uint32_t(i), uint32_t(c0 >> 2), a.step, 0u, a.seed, z);
-    const float h = a.h1[i];
+    // the pair's two normals: elements c0 & 3 and (c0 & 3) + 1 (c0 is even)
+    const float zp[2] = {(c0 & 2) ? z[2] : z[0], (c0 & 2) ? z[3] : z[1]};
+    const float h = hv[qq];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int r = r0 + u;
@@ -281,17 +317,17 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_sparse_euler_pair(StepArgs a, 
       const size_t og = size_t(r) * Np + i;
       const float xr = u == 0 ? x0[i] : x1[i];
       const float xi = CPLX ? x1[i] : 0.0f;
-      const float yr = u == 0 ? y0 : y1;
-      const float yi = CPLX ? y1 : 0.0f;
-      const float gs = a.gam[og];
+      const float yr = y[qq][u];
+      const float yi = CPLX ? y[qq][1] : 0.0f;
+      const float gs = gv[qq][u];
       float kr, ki, kg;
       gd_rhs(xr, xi, gs, yr, yi, s_beta[u], h, a.eps, a.rho_th, kr, ki, kg);
       if (CPLX && a.q) resonant_drive(xr, xi, a.q, a.hq, kr, ki);
       float nr = axpy(a.dt, kr, xr);
       float ni = axpy(a.dt, ki, xi);
       const float ng = axpy(a.dt, kg, gs);
-      nr = axpy(s_dsc[u], z[col & 3], nr);
-      if (CPLX) ni = axpy(s_dsc[u], z[(col + 1) & 3], ni);
+      nr = axpy(s_dsc[u], zp[u], nr);
+      if (CPLX) ni = axpy(s_dsc[u], zp[1], ni);
       a.psi_out[size_t(col) * Np + i] = nr;
       if (CPLX) a.psi_out[size_t(col + 1) * Np + i] = ni;
       a.gam[og] = ng;

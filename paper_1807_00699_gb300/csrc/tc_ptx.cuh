@@ -86,6 +86,14 @@ static __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorM
       : "memory");
 }
 
+// Untiled bulk copy of `bytes` (a multiple of 16) from global memory to this
+// CTA's shared memory, both addresses 16-byte aligned, completing on `bar`.
+static __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
 // L2 eviction policies (createpolicy): operand tiles that every step re-reads
 // are kept (evict_last); the FP32 state, streamed once per step, goes first.
 static __device__ __forceinline__ uint64_t policy_evict_last() {

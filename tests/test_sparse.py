@@ -52,7 +52,7 @@ def test_sparse_coupling_matches_oracle(gda, model, n, R):
 
 
 @pytest.mark.parametrize("integ", ["euler", "rk4"])
-@pytest.mark.parametrize("model,n,R", [("xy", 300, 40), ("ising", 258, 90)])
+@pytest.mark.parametrize("model,n,R", [("xy", 300, 40), ("ising", 258, 90), ("ising", 130, 33)])
 def test_sparse_200_steps_match_oracle(gda, integ, model, n, R):
     J = regular3(n, 7)
     g = 0.05 * synth.normal(8, n) if model == "ising" else synth.xy_gaussian(n, 8)[1]
@@ -70,26 +70,28 @@ def test_sparse_200_steps_match_oracle(gda, integ, model, n, R):
     s.close()
 
 
-def test_sparse_noise_decay_and_resume(gda):
+@pytest.mark.parametrize("model,R", [("xy", 24), ("ising", 23)])
+def test_sparse_noise_decay_and_resume(gda, model, R):
     # noise with decay uses the same density partial sums as the FP32 path;
     # resuming from a saved state is bit-identical to one run
-    n, R = 200, 24
+    n = 200
     J = regular3(n, 11)
     g = synth.xy_gaussian(n, 2)[1]
     kw = dict(dt=0.02, eps=0.2, noise_D=0.05, noise_decay=1, seed=77, prec=gda.SPARSE, init_amp=0.1)
-    a = gda.Solver(J, g, gda.XY)
+    m = gda.XY if model == "xy" else gda.ISING
+    a = gda.Solver(J, g, m)
     a.run(gda.default_params(init_mode=1, **kw), R, 60)
     full = a.get_state()
-    b = gda.Solver(J, g, gda.XY)
+    b = gda.Solver(J, g, m)
     b.run(gda.default_params(init_mode=1, **kw), R, 25)
     mid = b.get_state()
-    c = gda.Solver(J, g, gda.XY)
+    c = gda.Solver(J, g, m)
     c.set_state(mid[0], mid[1], mid[2], mid[3])
     c.run(gda.default_params(init_mode=2, **kw), R, 35)
     for x, y in zip(full[:3], c.get_state()[:3]):
         assert np.array_equal(x, y)
     pk = {k: v for k, v in kw.items() if k != "prec"}
-    ref = oracle.run(J, g, "xy", oracle.Params(init_mode=1, **pk), R, 60)[0]
+    ref = oracle.run(J, g, model, oracle.Params(init_mode=1, **pk), R, 60)[0]
     assert amp_err(full[0], ref) < 1e-4
     for s in (a, b, c):
         s.close()
