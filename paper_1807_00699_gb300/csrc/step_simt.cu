@@ -389,6 +389,10 @@ cudaError_t launch_sparse_w(const StepArgs& a, const Ell& ell, const float* oper
 cudaError_t launch_step_sparse(const StepArgs& a, const int* col, const float* val, const int* deg,
                                const float* operand, int maxdeg, cudaStream_t s) {
   const Ell ell{col, val, deg};
+  // the paper's 3-regular graphs: the staged Euler kernel loops over exactly
+  // three entries (a fourth slot would add a zero product and cost a load)
+  if (maxdeg <= 3 && a.mode == M_EULER && size_t(2) * a.Np * sizeof(float) <= kPairSmemMax)
+    return a.cplx ? launch_pair<true, 3>(a, ell, s) : launch_pair<false, 3>(a, ell, s);
   if (maxdeg <= 4) return launch_sparse_w<4>(a, ell, operand, s);
   if (maxdeg <= 8) return launch_sparse_w<8>(a, ell, operand, s);
   if (maxdeg <= 16) return launch_sparse_w<16>(a, ell, operand, s);
