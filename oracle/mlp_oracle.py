@@ -15,12 +15,18 @@ can be checked:
   target spins after the best global sign (Ising) or phase (XY), plus a
   weighted squared error of the instance-mean of outputs 2..4 against target
   settings;
-* one Adam step (Kingma & Ba, ICLR 2015) with bias correction.
+* one Adam step (Kingma & Ba, ICLR 2015) with bias correction;
+* the head that turns an instance's outputs into a start and settings: base
+  amplitudes amp * O[:, 0] (+ i amp * O[:, 1] for XY) and, with s the
+  logistic function and m the mean over the spins of O[:, 2:5],
+  eps = 0.02 + 0.48 s(m0), rho_th = 0.5 + 1.5 s(m1), beta0 = 0.1 + 0.9 s(m2).
 
 Pins (tests/test_oracle_mlp.py): finite differences of the loss through the
 forward pass check the hand-written backward pass; closed forms on tiny
 networks check the forward pass; the loss is checked for its symmetry and its
-minimum; the features are checked on a Mattis instance in closed form.
+minimum; the features are checked on a Mattis instance in closed form; the
+head's settings are checked at the logistic function's centre and limits, and
+for their invariance under a permutation or a repetition of the spins.
 """
 from __future__ import annotations
 
@@ -139,3 +145,14 @@ def adam_step(p, g, m1, m2, lr, b1, b2, eps, t):
     mh = m1 / (1 - b1 ** t)
     vh = m2 / (1 - b2 ** t)
     return p - lr * mh / (np.sqrt(vh) + eps), m1, m2
+
+
+def proposal_head(O: np.ndarray, cplx: bool, amp: float):
+    """(base, settings) of one instance from its outputs O [N][5]: base [N]
+    (complex for XY) and settings (eps, rho_th, beta0)."""
+    O = np.asarray(O, dtype=np.float64)
+    base = amp * O[:, 0] + (1j * amp * O[:, 1] if cplx else 0.0)
+    m = O[:, 2:5].mean(0)
+    sig = [1.0 / (1.0 + math.exp(-x)) for x in m]
+    settings = np.array([0.02 + 0.48 * sig[0], 0.5 + 1.5 * sig[1], 0.1 + 0.9 * sig[2]])
+    return base, settings

@@ -110,3 +110,29 @@ def test_adam_first_step_closed_form():
     q, m1, m2 = mo.adam_step(p, g, np.zeros(50), np.zeros(50), 0.01, 0.9, 0.999, 1e-8, 1)
     assert np.allclose(q, p - 0.01 * g / (np.abs(g) + 1e-8))
     assert np.allclose(m1, 0.1 * g) and np.allclose(m2, 0.001 * g * g)
+
+
+def test_proposal_head_centre_limits_and_invariances():
+    """The head's settings sit at the middle of their ranges for zero outputs,
+    at the ends for large outputs, and depend only on the spin-mean of the
+    outputs; the base is the scaled amplitude outputs."""
+    rng = np.random.default_rng(3)
+    O = np.zeros((7, 5))
+    _, st = mo.proposal_head(O, False, 0.1)
+    assert np.allclose(st, [0.26, 1.25, 0.55], rtol=0, atol=1e-15)
+    O[:, 2:5] = 50.0
+    assert np.allclose(mo.proposal_head(O, False, 0.1)[1], [0.5, 2.0, 1.0], atol=1e-15)
+    O[:, 2:5] = -50.0
+    assert np.allclose(mo.proposal_head(O, False, 0.1)[1], [0.02, 0.5, 0.1], atol=1e-15)
+    O = rng.normal(size=(40, 5))
+    b, st = mo.proposal_head(O, True, 0.25)
+    # one setting moved by one output alone: s(m) recovered from the setting
+    m = O[:, 2:5].mean(0)
+    assert np.isclose((st[0] - 0.02) / 0.48, 1 / (1 + np.exp(-m[0])), rtol=1e-14)
+    assert np.isclose((st[2] - 0.1) / 0.9, 1 / (1 + np.exp(-m[2])), rtol=1e-14)
+    perm = rng.permutation(40)
+    assert np.allclose(mo.proposal_head(O[perm], True, 0.25)[1], st, rtol=1e-14)
+    assert np.allclose(mo.proposal_head(np.concatenate([O, O]), True, 0.25)[1], st, rtol=1e-14)
+    assert np.array_equal(b, 0.25 * O[:, 0] + 0.25j * O[:, 1])
+    br, _ = mo.proposal_head(O, False, 0.25)
+    assert br.dtype == np.float64 and np.array_equal(br, 0.25 * O[:, 0])
