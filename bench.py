@@ -74,6 +74,11 @@ def parse():
     ap.add_argument("--timeline", action="store_true", help="kernel workload: per-CTA device timestamps")
     ap.add_argument("--sk-seeds", default="0", help="comma-separated instance seeds of the sk_quality workload")
     ap.add_argument("--batch-count", type=int, default=2000)
+    ap.add_argument("--batch-steps", type=int, default=2000, help="batched workload: GD steps per bench step")
+    ap.add_argument("--batch-schedule", default="auto", choices=["auto", "persistent", "per_step"],
+                    help="batched workload: launch schedule (auto: the autotuner's pick)")
+    ap.add_argument("--batch-bn", type=int, default=0, choices=[0, 128, 256],
+                    help="batched workload: tile width (0: the autotuner's pick)")
     return ap.parse_args()
 
 
@@ -281,8 +286,10 @@ def ttt_precisions(gda, torch, stream, W, J, g, model):
 def ttt_settings(gda, torch, stream):
     """XY N = 1000 (J ~ N(0, 1/N), g ~ U[-0.1, 0.1]), R = 1024, 20000 steps:
     the plain algorithm at its default settings, at the best fixed setting of
-    the proposal's grid (chosen on two other seeded instances), and with the
-    learned proposal (settings and start), in FP32 and BF16; each factor is
+    the proposal's grid (chosen on two other seeded instances), at the
+    network's mean settings on those two instances as fixed constants with the
+    plain start (does the proposal's per-instance output matter?), and with
+    the learned proposal (settings and start), in FP32 and BF16; each factor is
     varied alone against an arm that shares the rest."""
     import synth
     from paper_1807_00699_gb300 import proposal
@@ -292,10 +299,13 @@ def ttt_settings(gda, torch, stream):
     base = dict(dt=W["dt"], init_amp=W["init_amp"], seed=W["seed"], energy_every=W["energy_every"])
 
     # best fixed grid setting: calibrated on two other instances of the same family
+    prop = proposal.Proposal()
     calib = {}
+    const = []  # the network's settings on the calibration instances
     for cs in (2001, 2002):
         Jc, gc = synth.xy_gaussian(W["N"], cs)
         s = gda.Solver(Jc, gc, gda.XY, stream=stream)
+        const.append(prop.propose(s))
         runs = {}
         for k, (e, rho, b0) in enumerate(proposal.GRID):
             prm = proposal.run_params({"eps": e, "rho_th": rho, "beta0": b0}, init_mode=1, prec=gda.BF16, **base)
@@ -307,8 +317,8 @@ def ttt_settings(gda, torch, stream):
         s.close()
     k_fixed = min(calib, key=lambda k: (sum(x >= 10 ** 9 for x in calib[k]), float(np.mean(calib[k]))))
     fixed = dict(zip(("eps", "rho_th", "beta0"), proposal.GRID[k_fixed]))
+    learned_const = {k: float(np.mean([c[k] for c in const])) for k in ("eps", "rho_th", "beta0")}
 
-    prop = proposal.Proposal()
     s = gda.Solver(J, g, gda.XY, stream=stream)
     s32 = gda.Solver(J, g, gda.XY, stream=stream)
     plain = dict(eps=W["eps"], rho_th=W["rho_th"], beta0=W["beta0"], eps_hat=W["eps_hat"])
@@ -320,6 +330,8 @@ def ttt_settings(gda, torch, stream):
                                  R, steps)
     arms["bf16_best_fixed"] = ttt_arm(torch, stream, s, proposal.run_params(fixed, init_mode=1, prec=gda.BF16, **base),
                                       R, steps)
+    arms["bf16_learned_const"] = ttt_arm(torch, stream, s,
+                                         proposal.run_params(learned_const, init_mode=1, prec=gda.BF16, **base), R, steps)
 
     def learned(solver, prec):
         def pre():
@@ -339,8 +351,9 @@ def ttt_settings(gda, torch, stream):
     s.close()
     s32.close()
     out["best_fixed_setting"] = {**fixed, "grid_index": k_fixed, "calibration_steps_to_target": calib[k_fixed]}
+    out["learned_const_setting"] = learned_const
     for name in ("bf16_learned", "bf16_batched_learned"):
-        for ref in ("fp32_plain", "bf16_best_fixed", "bf16_plain"):
+        for ref in ("fp32_plain", "bf16_best_fixed", "bf16_plain", "bf16_learned_const"):
             if name in out and out[name]["ttt_s"] and out[ref]["ttt_s"]:
                 out[f"speedup_{name}_vs_{ref}"] = out[ref]["ttt_s"] / out[name]["ttt_s"]
     return out
@@ -561,12 +574,15 @@ def run_batched(args):
     # the unnormalised {-1, 0, +1} couplings reach |lambda| ~ 2 sqrt(N / 2) ~ 63 at
     # N = 2000, where forward Euler stays stable at dt = 0.005 (diverges at 0.01)
     p = gda.default_params(dt=0.005, eps=0.1, init_mode=1, init_amp=1e-3, prec=gda.BF16)
-    steps = 2000
-    # autotune the tile width and the launch schedule on 200 steps
+    steps = args.batch_steps
+    # autotune the tile width and the launch schedule on 200 steps (over the
+    # choices the command line leaves open)
     tune = {}
-    for sched in ("persistent", "per_step"):
+    scheds = ("persistent", "per_step") if args.batch_schedule == "auto" else (args.batch_schedule,)
+    bns = (128, 256) if args.batch_bn == 0 else (args.batch_bn,)
+    for sched in scheds if len(scheds) * len(bns) > 1 else ():
         b.set_schedule(gda.RESIDENT if sched == "persistent" else gda.PER_STEP)
-        for bn in (128, 256):
+        for bn in bns:
             b.set_tile(bn)
             b.run(p, 200)
             e0 = torch.cuda.Event(enable_timing=True)
@@ -576,7 +592,7 @@ def run_batched(args):
             e1.record(stream)
             e1.synchronize()
             tune[f"{sched}_bn{bn}"] = e0.elapsed_time(e1) / 1e3 / 200
-    best = min(tune, key=tune.get)
+    best = min(tune, key=tune.get) if tune else f"{scheds[0]}_bn{bns[0]}"
     sched, bn = best.split("_bn")[0], int(best.split("_bn")[1])
     b.set_schedule(gda.RESIDENT if sched == "persistent" else gda.PER_STEP)
     b.set_tile(bn)

@@ -391,6 +391,19 @@ gda_status gda_proposal_loss(const float* O, const float* S, const float* Tset, 
                              const int32_t* cplx, int32_t n_inst, float wset, float* dO, float* loss,
                              void* stream);
 
+/* The proposal's head, on the device, for one instance of N spins: from the
+ * network outputs O [N][5] (gda_mlp_forward), the init_mode 3 base amplitudes
+ * for gda_set_init_base / gda_batch_set_init_base with on_device = 1 --
+ * base [N] = amp * O[:, 0] (Ising, cplx = 0) or base [N][2] = amp * (O[:, 0],
+ * O[:, 1]) (XY), each the float rounding of the double product -- and the
+ * instance's settings [3] (double) = (eps, rho_th, beta0) =
+ * (0.02 + 0.48 s(m0), 0.5 + 1.5 s(m1), 0.1 + 0.9 s(m2)), s the logistic
+ * function, m_k the mean over the spins of O[:, 2 + k] (summed in double).
+ * Device pointers, owned by the caller; asynchronous on `stream`.
+ * GDA_ERR_INVALID for a null pointer or N < 1. */
+gda_status gda_proposal_head(const float* O, int32_t N, int32_t cplx, double amp, float* base, double* settings,
+                             void* stream);
+
 /* One Adam step (bias corrected, step t >= 1) on P parameters. */
 gda_status gda_adam_step(float* params, const float* grad, float* m1, float* m2, int32_t P, float lr,
                          float beta1, float beta2, float eps, int32_t t, void* stream);

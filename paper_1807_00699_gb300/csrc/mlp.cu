@@ -260,6 +260,45 @@ __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float
   }
 }
 
+// The proposal's head for one instance (one block): base amplitudes
+// amp * O[:, 0] (+ the imaginary part amp * O[:, 1], interleaved, for XY),
+// each the float rounding of the double product, and the settings from the
+// spin-means of outputs 2..4 (double sums in a fixed tree order):
+// eps = 0.02 + 0.48 s(m0), rho_th = 0.5 + 1.5 s(m1), beta0 = 0.1 + 0.9 s(m2),
+// s the logistic function.
+constexpr int HEAD_THREADS = 256;
+__global__ void __launch_bounds__(HEAD_THREADS) k_proposal_head(const float* __restrict__ O, int N, int cplx,
+                                                               double amp, float* __restrict__ base,
+                                                               double* __restrict__ settings) {
+  __shared__ double red[3][HEAD_THREADS];
+  const int t = threadIdx.x;
+  double m[3] = {0.0, 0.0, 0.0};
+  for (int i = t; i < N; i += HEAD_THREADS) {
+    const float* o = O + size_t(i) * DOUT;
+    if (cplx) {
+      base[2 * size_t(i)] = float(amp * double(o[0]));
+      base[2 * size_t(i) + 1] = float(amp * double(o[1]));
+    } else {
+      base[i] = float(amp * double(o[0]));
+    }
+    for (int k = 0; k < 3; ++k) m[k] += double(o[2 + k]);
+  }
+  for (int k = 0; k < 3; ++k) red[k][t] = m[k];
+  __syncthreads();
+  for (int w = HEAD_THREADS / 2; w > 0; w >>= 1) {
+    if (t < w)
+      for (int k = 0; k < 3; ++k) red[k][t] += red[k][t + w];
+    __syncthreads();
+  }
+  if (t == 0) {
+    const double lo[3] = {0.02, 0.5, 0.1}, span[3] = {0.48, 1.5, 0.9};
+    for (int k = 0; k < 3; ++k) {
+      const double mean = N > 0 ? red[k][0] / double(N) : 0.0;
+      settings[k] = lo[k] + span[k] * (1.0 / (1.0 + exp(-mean)));
+    }
+  }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------- features
@@ -411,5 +450,13 @@ extern "C" gda_status gda_adam_step(float* params, const float* grad, float* m1,
   if (!params || !grad || !m1 || !m2 || P < 0 || t < 1) return GDA_ERR_INVALID;
   k_adam<<<(P + 255) / 256, 256, 0, static_cast<cudaStream_t>(stream)>>>(params, grad, m1, m2, P, lr, beta1, beta2,
                                                                           eps, t);
+  return cudaGetLastError() == cudaSuccess ? GDA_OK : GDA_ERR_CUDA;
+}
+
+extern "C" gda_status gda_proposal_head(const float* O, int32_t N, int32_t cplx, double amp, float* base,
+                                        double* settings, void* stream) {
+  if (!O || !base || !settings || N < 1) return GDA_ERR_INVALID;
+  k_proposal_head<<<1, HEAD_THREADS, 0, static_cast<cudaStream_t>(stream)>>>(O, N, cplx ? 1 : 0, amp, base,
+                                                                             settings);
   return cudaGetLastError() == cudaSuccess ? GDA_OK : GDA_ERR_CUDA;
 }

@@ -66,6 +66,7 @@ SIGNATURES = {
     "gda_mlp_forward": (ct.c_int, [_VP, _VP, ct.c_int32, _VP, _VP, _VP]),
     "gda_mlp_backward": (ct.c_int, [_VP, _VP, _VP, _VP, ct.c_int32, _VP, _VP]),
     "gda_proposal_loss": (ct.c_int, [_VP, _VP, _VP, _VP, _VP, ct.c_int32, ct.c_float, _VP, _VP, _VP]),
+    "gda_proposal_head": (ct.c_int, [_VP, ct.c_int32, ct.c_int32, ct.c_double, _VP, _VP, _VP]),
     "gda_adam_step": (ct.c_int, [_VP, _VP, _VP, _VP, ct.c_int32, ct.c_float, ct.c_float, ct.c_float, ct.c_float,
                                  ct.c_int32, _VP]),
     "gda_batch_create": (ct.c_int, [ct.c_int32, ct.POINTER(ct.c_int32), ct.POINTER(ct.c_int32), ct.POINTER(ct.c_int32),
@@ -291,6 +292,11 @@ class Solver:
             flat = np.ascontiguousarray(base.real, dtype=np.float32)
         self._check(self._lib.gda_set_init_base(self._h, flat.ctypes.data_as(_VP), 0))
 
+    def set_init_base_dev(self, base_ptr: int):
+        """init_mode 3 base amplitudes from a device buffer in
+        gda_set_init_base's layout (e.g. gda_proposal_head's output)."""
+        self._check(self._lib.gda_set_init_base(self._h, _VP(base_ptr), 1))
+
     def features(self, F_ptr: int):
         """Per-spin features [N][8] into a device buffer (see gda_features)."""
         self._check(self._lib.gda_features(self._h, _VP(F_ptr)))
@@ -373,6 +379,10 @@ class Batch:
         else:
             flat = np.ascontiguousarray(base.real, dtype=np.float32)
         self._check(self._lib.gda_batch_set_init_base(self._h, int(k), flat.ctypes.data_as(_VP), 0))
+
+    def set_init_base_dev(self, k: int, base_ptr: int):
+        """Instance k's init_mode 3 base amplitudes from a device buffer."""
+        self._check(self._lib.gda_batch_set_init_base(self._h, int(k), _VP(base_ptr), 1))
 
     def launch_mode(self) -> int:
         """1: chunks replay a captured CUDA graph; 0: direct launches."""

@@ -89,12 +89,34 @@ class Proposal:
         torch.cuda.synchronize()
         return O.cpu().numpy().astype(np.float64)
 
+    def head(self, solver: "gda.Solver"):
+        """Features, network and head (gda_proposal_head) on the device for
+        the solver's instance: (base, settings), base a device tensor in
+        gda_set_init_base's layout; the settings (24 bytes) are the only data
+        read back to the host."""
+        torch = self.torch
+        N = solver.N
+        xy = solver.model == gda.XY
+        F = torch.empty((N, 8), dtype=torch.float32, device="cuda")
+        O = torch.empty((N, 5), dtype=torch.float32, device="cuda")
+        base = torch.empty(2 * N if xy else N, dtype=torch.float32, device="cuda")
+        st = torch.empty(3, dtype=torch.float64, device="cuda")
+        solver.features(F.data_ptr())  # on the solver's stream
+        torch.cuda.synchronize()
+        s = ct.c_void_p(torch.cuda.current_stream().cuda_stream)
+        vp = lambda x: ct.c_void_p(x.data_ptr())  # noqa: E731
+        r = self.lib.gda_mlp_forward(vp(self.p), vp(F), N, vp(O), None, s)
+        if r == 0:
+            r = self.lib.gda_proposal_head(vp(O), N, 1 if xy else 0, AMP, vp(base), vp(st), s)
+        if r != 0:
+            raise gda.GdaError(r, "proposal kernels failed")
+        v = st.cpu().tolist()
+        return base, {"eps": v[0], "rho_th": v[1], "beta0": v[2]}
+
     def propose(self, solver: "gda.Solver"):
         """Sets the solver's init_mode-3 base amplitudes and returns the settings."""
-        O = self.outputs(solver)
-        settings = settings_from_outputs(O[:, 2:5].mean(0))
-        xy = solver.model == gda.XY
-        solver.set_init_base(AMP * (O[:, 0] + (1j * O[:, 1] if xy else 0.0)))
+        base, settings = self.head(solver)
+        solver.set_init_base_dev(base.data_ptr())
         return settings
 
 
@@ -102,10 +124,8 @@ def propose_into_batch(prop: "Proposal", solver: "gda.Solver", batch: "gda.Batch
     """The proposal for the instance of `solver`, given to instance k of a
     batch: its settings (gda_batch_set_params, with the batch step dt) and
     its init_mode-3 base amplitudes.  Returns the settings."""
-    O = prop.outputs(solver)
-    settings = settings_from_outputs(O[:, 2:5].mean(0))
-    xy = solver.model == gda.XY
-    batch.set_init_base(k, AMP * (O[:, 0] + (1j * O[:, 1] if xy else 0.0)))
+    base, settings = prop.head(solver)
+    batch.set_init_base_dev(k, base.data_ptr())
     batch.set_params(k, run_params(settings, dt=dt))
     return settings
 
@@ -295,29 +315,46 @@ def best_fixed_setting(model: str, n: int, seeds, R=64, nsteps=5000, every=25, d
     return GRID[k_best]
 
 
-def evaluate(prop: Proposal, cases, R=64, nsteps=5000, every=25, fixed=None, log=print):
-    """FP64-verified time to target of three arms on held-out seeds, BF16, same
-    R and steps: plain GD (default settings, small random start), plain GD at
+def mean_proposed_setting(prop: Proposal, model: str, n: int, seeds) -> dict:
+    """The network's settings averaged over instances of the family that the
+    evaluation does not use: the proposal reduced to per-model constants."""
+    got = []
+    for seed in seeds:
+        J, g = eval_instance(model, n, seed)
+        s = gda.Solver(J, g, gda.XY if model == "xy" else gda.ISING)
+        got.append(prop.propose(s))
+        s.close()
+    return {k: float(np.mean([x[k] for x in got])) for k in ("eps", "rho_th", "beta0")}
+
+
+def evaluate(prop: Proposal, cases, R=64, nsteps=5000, every=25, fixed=None, const=None, log=print):
+    """FP64-verified time to target on held-out seeds, BF16, same R and steps,
+    of the arms: plain GD (default settings, small random start), plain GD at
     the best fixed grid setting for the model (fixed[model], from
-    best_fixed_setting), and the proposal (its settings and start).  The
-    target is within 1e-3 of the best FP64 energy any arm reached (final
-    restarts or traced configurations); an arm hits it at the first trace
-    point whose named configuration is at or below it in FP64."""
+    best_fixed_setting), plain GD at the network's mean settings as constants
+    (const[model], from mean_proposed_setting: an ablation of the per-instance
+    output and of the proposed start), and the proposal (its settings and
+    start).  The target is within 1e-3 of the best FP64 energy any arm reached
+    (final restarts or traced configurations); an arm hits it at the first
+    trace point whose named configuration is at or below it in FP64."""
     rows = []
     for model, n, seed in cases:
         J, g = eval_instance(model, n, seed)
         xy = model == "xy"
         s = gda.Solver(J, g, gda.XY if xy else gda.ISING)
         res = {}
-        arms = ["plain", "learned"] + (["best_fixed"] if fixed else [])
+        arms = ["plain", "learned"] + (["best_fixed"] if fixed else []) + (["learned_const"] if const else [])
         for arm in arms:
             if arm == "plain":
                 settings = {"eps": 0.1, "rho_th": 1.0, "beta0": 1.0}
                 prm = gda.default_params(dt=0.05, eps=0.1, rho_th=1.0, init_mode=1, init_amp=1e-3, seed=seed,
                                          prec=gda.BF16, energy_every=every)
-            elif arm == "best_fixed":
-                e, rho, b0 = fixed[model]
-                settings = {"eps": e, "rho_th": rho, "beta0": b0}
+            elif arm in ("best_fixed", "learned_const"):
+                if arm == "best_fixed":
+                    e, rho, b0 = fixed[model]
+                    settings = {"eps": e, "rho_th": rho, "beta0": b0}
+                else:
+                    settings = dict(const[model])
                 prm = run_params(settings, dt=0.05, init_mode=1, init_amp=1e-3, seed=seed, prec=gda.BF16,
                                  energy_every=every)
             else:
@@ -362,8 +399,11 @@ def main(argv=None):
         prop = Proposal(np.load(a.out))
         fixed = {"xy": best_fixed_setting("xy", 1024, [2 * 10 ** 6, 2 * 10 ** 6 + 1]),
                  "ising": best_fixed_setting("ising", 2048, [2 * 10 ** 6 + 100, 2 * 10 ** 6 + 101])}
+        const = {"xy": mean_proposed_setting(prop, "xy", 1024, [2 * 10 ** 6, 2 * 10 ** 6 + 1]),
+                 "ising": mean_proposed_setting(prop, "ising", 2048, [2 * 10 ** 6 + 100, 2 * 10 ** 6 + 101])}
         cases = [("xy", 1024, 10 ** 6 + k) for k in range(4)] + [("ising", 2048, 10 ** 6 + 100 + k) for k in range(4)]
-        report = {"best_fixed": fixed, "eval": evaluate(prop, cases, fixed=fixed)}
+        report = {"best_fixed": fixed, "learned_const": const,
+                  "eval": evaluate(prop, cases, fixed=fixed, const=const)}
     if a.report:
         with open(a.report, "w") as fh:
             json.dump(report, fh, indent=1, default=float)

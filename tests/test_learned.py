@@ -113,6 +113,36 @@ def test_short_training_reduces_loss(env):
     assert losses[-1] < 0.7 * losses[0]
 
 
+@pytest.mark.parametrize("model,n", [("xy", 300), ("ising", 517), ("ising", 1)])
+def test_proposal_head_matches_oracle(env, model, n):
+    """gda_proposal_head (base amplitudes and settings on the device) against
+    the oracle's head on the same network outputs; the solver's init_mode 3
+    start then equals the one set from the host."""
+    torch, gda, lib = env
+    from paper_1807_00699_gb300 import proposal
+    xy = model == "xy"
+    J, g = synth.xy_gaussian(n, 12)
+    s = gda.Solver(J, g if xy else np.zeros(n), gda.XY if xy else gda.ISING)
+    prop = proposal.Proposal()
+    O = prop.outputs(s)
+    base, st = prop.head(s)
+    rb, rs = mo.proposal_head(O, xy, proposal.AMP)
+    want = np.stack([rb.real, rb.imag], -1).ravel() if xy else rb
+    assert np.array_equal(base.cpu().numpy(), want.astype(np.float32))
+    got = np.array([st["eps"], st["rho_th"], st["beta0"]])
+    assert np.allclose(got, rs, rtol=1e-12, atol=0)
+    # the start set from the device equals the start set from the host
+    kw = dict(dt=0.05, eps=0.1, init_mode=3, init_amp=proposal.AMP, seed=4, prec=gda.FP32)
+    s.set_init_base_dev(base.data_ptr())
+    s.run(gda.default_params(**kw), 8, 0)
+    a = s.get_state()[0]
+    s.set_init_base(rb)
+    s.run(gda.default_params(**kw), 8, 0)
+    assert np.array_equal(a, s.get_state()[0])
+    s.close()
+    assert lib.gda_proposal_head(None, n, 0, 0.1, None, None, None) == 1  # GDA_ERR_INVALID
+
+
 def test_trained_proposal_gain_over_best_fixed_setting(env):
     """The committed network on held-out seeds (XY N = 1024, Ising N = 2048,
     J ~ N(0, 1/N)) against plain GD at its default settings and at the best
