@@ -66,7 +66,8 @@ def parse():
                          "sparse 3-regular graphs (weights U[a, b], a, b in {-10, -3, 3, 10})")
     ap.add_argument("--n", type=int, default=1000, help="kernel workload: spins")
     ap.add_argument("--r", type=int, default=1024, help="kernel workload: restarts")
-    ap.add_argument("--sched", default="auto", choices=["auto", "per_step", "resident", "pair", "stream", "stream_pair"])
+    ap.add_argument("--sched", default="auto",
+                    choices=["auto", "per_step", "resident", "pair", "stream", "stream_pair", "resident_pair"])
     ap.add_argument("--integ", default="euler", choices=["euler", "rk4"])
     ap.add_argument("--coupling", default="gd", choices=["gd", "gdmod"],
                     help="kernel workload: GD (K = beta J) or GD-mod (per-restart K, FP32)")
@@ -762,7 +763,7 @@ def run_kernel(args):
         dt = 0.1 / math.sqrt(N)
     prec = {"fp32": gda.FP32, "bf16": gda.BF16, "fp8": gda.FP8, "sparse": gda.SPARSE}[args.prec]
     sched = {"auto": gda.AUTO, "per_step": gda.PER_STEP, "resident": gda.RESIDENT, "pair": gda.PAIR,
-             "stream": gda.STREAM, "stream_pair": gda.STREAM_PAIR}[args.sched]
+             "stream": gda.STREAM, "stream_pair": gda.STREAM_PAIR, "resident_pair": gda.RESIDENT_PAIR}[args.sched]
     integ = gda.RK4 if args.integ == "rk4" else gda.EULER
     stream = torch.cuda.Stream()
     s = gda.Solver(J, g, gda.XY if args.model == "xy" else gda.ISING, stream=stream)

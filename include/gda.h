@@ -182,8 +182,15 @@ typedef enum {
                               * epilogues of the step before (two-SM tiles where
                               * AUTO would take them); GDA_ERR_UNSUPPORTED for
                               * RK4 or FP32 */,
-  GDA_SCHEDULE_STREAM_PAIR = 5 /* GDA_SCHEDULE_STREAM with two-SM tiles always
+  GDA_SCHEDULE_STREAM_PAIR = 5, /* GDA_SCHEDULE_STREAM with two-SM tiles always
                               * (conditions of GDA_SCHEDULE_PAIR) */
+  GDA_SCHEDULE_RESIDENT_PAIR = 6 /* the resident kernel with two-SM tiles: the
+                              * CTAs of row blocks 2p, 2p + 1 form a cluster and
+                              * share M = 256 tensor-core instructions, each
+                              * keeping its own rows' state in tensor memory;
+                              * conditions of GDA_SCHEDULE_RESIDENT plus an even
+                              * number of 128-row blocks and every cluster
+                              * resident at once, else GDA_ERR_UNSUPPORTED */
 } gda_schedule;
 
 /* Fills p with dt = 0.01, eps = 0.1, rho_th = 1, gamma0 = 0, beta0 = 1,

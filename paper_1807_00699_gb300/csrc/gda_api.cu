@@ -343,11 +343,12 @@ gda_status check_params(gda_ctx* c, const gda_params* p) {
   if (p->init_mode < 0 || p->init_mode > 3) return fail(c, GDA_ERR_INVALID, "init_mode must be 0, 1, 2 or 3");
   if (p->init_mode == 3 && !c->base) return fail(c, GDA_ERR_STATE, "init_mode 3 needs gda_set_init_base first");
   if (p->energy_every < 0) return fail(c, GDA_ERR_INVALID, "energy_every must be >= 0");
-  if (p->schedule < GDA_SCHEDULE_AUTO || p->schedule > GDA_SCHEDULE_STREAM_PAIR)
+  if (p->schedule < GDA_SCHEDULE_AUTO || p->schedule > GDA_SCHEDULE_RESIDENT_PAIR)
     return fail(c, GDA_ERR_INVALID, "unknown schedule %d", p->schedule);
   if ((p->prec == GDA_BF16 || p->prec == GDA_FP8) && !c->tc_ok)
     return fail(c, GDA_ERR_UNSUPPORTED, "tensor-core path needs an sm_103 device");
-  if (p->prec == GDA_SPARSE && p->schedule == GDA_SCHEDULE_RESIDENT)
+  const bool res_sched = p->schedule == GDA_SCHEDULE_RESIDENT || p->schedule == GDA_SCHEDULE_RESIDENT_PAIR;
+  if (p->prec == GDA_SPARSE && res_sched)
     return fail(c, GDA_ERR_UNSUPPORTED, "the sparse product runs per step");
   if ((p->schedule == GDA_SCHEDULE_PAIR || p->schedule == GDA_SCHEDULE_STREAM_PAIR) &&
       (!(p->prec == GDA_BF16 || p->prec == GDA_FP8) || (c->Np / 128) % 2 != 0 || p->coupling != GDA_COUPLING_GD))
@@ -360,13 +361,13 @@ gda_status check_params(gda_ctx* c, const gda_params* p) {
     return fail(c, GDA_ERR_INVALID, "wait_s must be in [0, 1000] seconds");
   if (p->withhold_flag < 0) return fail(c, GDA_ERR_INVALID, "withhold_flag must be >= 0");
   if (!finite(p->hq)) return fail(c, GDA_ERR_INVALID, "non-finite hq");
-  if (p->q != 0 && (!c->cplx || p->schedule == GDA_SCHEDULE_RESIDENT || p->coupling == GDA_COUPLING_GDMOD))
+  if (p->q != 0 && (!c->cplx || res_sched || p->coupling == GDA_COUPLING_GDMOD))
     return fail(c, GDA_ERR_UNSUPPORTED, "the resonant drive needs complex amplitudes (GDA_XY) and per-step GD");
   if (p->coupling != GDA_COUPLING_GD && p->coupling != GDA_COUPLING_GDMOD)
     return fail(c, GDA_ERR_INVALID, "unknown coupling mode %d", p->coupling);
   if (p->coupling == GDA_COUPLING_GDMOD) {
     if (!finite(p->gamma_c)) return fail(c, GDA_ERR_INVALID, "non-finite gamma_c");
-    if (p->prec != GDA_FP32 || p->integ != GDA_EULER || p->schedule == GDA_SCHEDULE_RESIDENT)
+    if (p->prec != GDA_FP32 || p->integ != GDA_EULER || res_sched)
       return fail(c, GDA_ERR_UNSUPPORTED, "GD-mod runs FP32 forward Euler, per step");
     if (p->noise_D != 0.0 && p->noise_decay) return fail(c, GDA_ERR_UNSUPPORTED, "GD-mod has no noise decay");
     if (gdmod_smem_bytes(c->Np, c->cplx) > 227 * 1024) return fail(c, GDA_ERR_UNSUPPORTED, "N too large for GD-mod");
@@ -743,11 +744,17 @@ gda_status gda_run(gda_ctx* c, const gda_params* p, int32_t R, int64_t steps) {
   const size_t opsz = cn;
   // Resident persistent kernel: BF16 Euler runs whose tiles all fit on the
   // device at once run as one launch per tracking segment.
-  const bool resident = p->prec == GDA_BF16 && p->integ == GDA_EULER && p->q == 0 && (p->schedule == GDA_SCHEDULE_AUTO || p->schedule == GDA_SCHEDULE_RESIDENT) &&
+  const bool res_sched = p->schedule == GDA_SCHEDULE_AUTO || p->schedule == GDA_SCHEDULE_RESIDENT ||
+                         p->schedule == GDA_SCHEDULE_RESIDENT_PAIR;
+  const bool resident = p->prec == GDA_BF16 && p->integ == GDA_EULER && p->q == 0 && res_sched &&
                         res_fits(c->N, c->C, c->dev) &&
                         (long long)((c->C + 127) / 128) * ((c->N + 127) / 128) <= kMaxResidentTiles;
-  if (p->schedule == GDA_SCHEDULE_RESIDENT && !resident)
+  if ((p->schedule == GDA_SCHEDULE_RESIDENT || p->schedule == GDA_SCHEDULE_RESIDENT_PAIR) && !resident)
     return fail(c, GDA_ERR_UNSUPPORTED, "resident schedule needs BF16, Euler and a grid that fits the device");
+  // two-SM tiles in the resident kernel: on request
+  const bool res_pair = resident && p->schedule == GDA_SCHEDULE_RESIDENT_PAIR;
+  if (res_pair && !res_pair_fits(c->N, c->C))
+    return fail(c, GDA_ERR_UNSUPPORTED, "two-SM resident tiles need an even number of 128-row blocks and room for every cluster");
   if (tc && !resident && (p->schedule == GDA_SCHEDULE_AUTO || p->schedule == GDA_SCHEDULE_STREAM) &&
       tc_pair_pays(c->N, c->C))
     c->run_pair = true;
@@ -832,7 +839,7 @@ gda_status gda_run(gda_ctx* c, const gda_params* p, int32_t R, int64_t steps) {
       ra.withhold_tile = p->withhold_flag > 0 ? int((c->C + 127) / 128) * int((c->N + 127) / 128) - 1 : -1;
       ra.withhold_step = p->withhold_flag > 0 ? p->withhold_flag : -1;
       CK(cudaMemsetAsync(c->flags, 0, kMaxResidentTiles * sizeof(unsigned), c->stream));
-      LK(launch_step_res(c->plan, ra, a, c->stream));
+      LK(launch_step_res(c->plan, ra, a, c->stream, res_pair));
       c->cur ^= flip;
       c->bcur ^= flip;
       c->opcur ^= flip;

@@ -21,8 +21,12 @@ struct ResArgs {
 
 // True if every CTA of the launch for N spins and C columns fits on the device at once.
 bool res_fits(int N, int C, int device);
-cudaError_t launch_step_res(const TcPlan* plan, const ResArgs& ra, const StepArgs& a, cudaStream_t s);
+// The same for the two-SM form (clusters of two row blocks; the current
+// device): an even number of row blocks and every cluster resident at once.
+bool res_pair_fits(int N, int C);
+cudaError_t launch_step_res(const TcPlan* plan, const ResArgs& ra, const StepArgs& a, cudaStream_t s, bool pair);
 const CUtensorMap* tc_plan_A(const TcPlan* plan);
-const CUtensorMap* tc_plan_B(const TcPlan* plan);
+const CUtensorMap* tc_plan_B(const TcPlan* plan);    // 128-row operand boxes
+const CUtensorMap* tc_plan_B64(const TcPlan* plan);  // 64-row operand boxes (halves of a pair's tile)
 
 }  // namespace gda

@@ -14,6 +14,13 @@
 //
 // Roles: warp 0 TMA producer; warp 1 TMEM allocator + MMA issuer; warps 2..17
 // epilogue (warp w reads TMEM lane quarter w % 4 and a quarter of the columns).
+//
+// PAIR form: the CTAs of row blocks 2p and 2p + 1 of a column block run as a
+// cluster of two, and the even CTA issues M = 256 tcgen05.mma.cta_group::2
+// instructions over both CTAs' shared memory.  Each CTA loads its own 128 rows
+// of the coupling tile and half (64 columns) of the operand tile, and receives
+// its own rows of the accumulator in its tensor memory, where its state stays;
+// the K loop moves a quarter fewer bytes through each SM's shared memory.
 // Per-element arithmetic is the Euler update of Eqs. (2), (5), (6) with the
 // same FP32 expression sequence as the per-step kernels.
 #include "tc_epilogue.cuh"
@@ -28,15 +35,22 @@ constexpr int EPI_WARPS = 16;                 // 4 per tensor-memory lane quarte
 constexpr int RES_THREADS = 64 + 32 * EPI_WARPS;
 constexpr int CPT = 128 / (EPI_WARPS / 4);    // columns per epilogue thread
 constexpr int BN = 128;
-constexpr int STAGES = 6;
 constexpr uint32_t A_BYTES = BM * BK * 2;
-constexpr uint32_t B_BYTES = BN * BK * 2;
-constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr uint32_t TMEM_COLS = 512;
 constexpr uint32_t T_PSI = 128;  // tensor-memory column of psi
 constexpr uint32_t T_GAM = 256;  // tensor-memory column of gamma
-constexpr uint32_t TAIL = (2 * STAGES + 2) * 8 + 8 * BN * 4 + 16;
-constexpr uint32_t SMEM = 1024 + STAGES * STAGE_BYTES + TAIL;
+// The ring of one CTA: a one-SM tile loads the whole 128-column operand slice
+// of a K-block, a CTA of a pair its 64-column half, so its stages are smaller
+// and its ring deeper.
+template <bool PAIR>
+struct ResCfg {
+  static constexpr int STAGES = PAIR ? 8 : 6;
+  static constexpr int BH = PAIR ? BN / 2 : BN;  // operand columns loaded by this CTA
+  static constexpr uint32_t B_BYTES = BH * BK * 2;
+  static constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
+  static constexpr uint32_t TAIL = (2 * STAGES + 2) * 8 + 8 * BN * 4 + 16;
+  static constexpr uint32_t SMEM = 1024 + STAGES * STAGE_BYTES + TAIL;
+};
 
 __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"n"(32 * EPI_WARPS) : "memory"); }
 
@@ -50,10 +64,14 @@ __device__ __forceinline__ bool flag_wait(const unsigned* f, unsigned target, lo
   return true;
 }
 
-template <bool CPLX>
+template <bool CPLX, bool PAIR>
 __global__ void __launch_bounds__(RES_THREADS, 1)
     step_res_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, ResArgs ra,
                     StepArgs a) {
+  using Cfg = ResCfg<PAIR>;
+  constexpr int STAGES = Cfg::STAGES;
+  constexpr uint32_t B_BYTES = Cfg::B_BYTES;
+  constexpr uint32_t STAGE_BYTES = Cfg::STAGE_BYTES;
   constexpr int W = CPLX ? 2 : 1;
   constexpr int RPT = BN / W;
   constexpr int CW = 8;                 // columns per epilogue chunk
@@ -77,6 +95,8 @@ __global__ void __launch_bounds__(RES_THREADS, 1)
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
   const int KB = (a.N + BK - 1) / BK;
   const long long lim = a.wait_cycles;
+  const uint32_t rank = PAIR ? cluster_ctarank() : 0u;  // the odd row block of a pair: 1
+  const bool leader = rank == 0;
   auto full_bar = [&](int s) { return smem_u32(bars + s); };
   auto empty_bar = [&](int s) { return smem_u32(bars + STAGES + s); };
   const uint32_t acc_full = smem_u32(bars + 2 * STAGES);
@@ -89,14 +109,20 @@ __global__ void __launch_bounds__(RES_THREADS, 1)
       mbar_init(empty_bar(s), 1);
     }
     mbar_init(acc_full, 1);
-    mbar_init(acc_free, 1);
+    mbar_init(acc_free, PAIR ? 2 : 1);  // both CTAs' epilogues free a pair's accumulator
     s_flag[0] = 0;
     s_flag[1] = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 1) tmem_alloc(smem_u32(s_tmem), TMEM_COLS);
+  if (warp == 1) {
+    if (PAIR)
+      tmem_alloc_pair(smem_u32(s_tmem), TMEM_COLS);
+    else
+      tmem_alloc(smem_u32(s_tmem), TMEM_COLS);
+  }
   tc_fence_before();
   __syncthreads();
+  if (PAIR) cluster_sync();  // barriers of both CTAs initialised before any remote arrival
   tc_fence_after();
   const uint32_t tmem = *s_tmem;
   if (threadIdx.x == 0) stamp(a, 1);
@@ -109,9 +135,26 @@ __global__ void __launch_bounds__(RES_THREADS, 1)
       const unsigned* col_flags = ra.flags + size_t(blockIdx.x) * gridDim.y;
       // ring slots [a_lo, a_hi) have their A tile issued but not yet their B tile
       int a_lo = 0, a_hi = 0, brow = 0;
+      // a stage's copies: the A tile arms the stage (a pair's even CTA counts
+      // both CTAs' bytes on its own barrier), the B tile follows
+      auto issue_a = [&](int s, int kb) {
+        if (PAIR) {
+          if (leader) mbar_arrive_expect_tx(full_bar(s), 2 * STAGE_BYTES);
+          tma_load_2d_pair(sA + s * A_BYTES, &tmA, kb * BK, m0, mapa_shared(full_bar(s), 0));
+        } else {
+          mbar_arrive_expect_tx(full_bar(s), STAGE_BYTES);
+          tma_load_2d(sA + s * A_BYTES, &tmA, kb * BK, m0, full_bar(s));
+        }
+      };
+      auto issue_b = [&](int s, int kb) {
+        if (PAIR)
+          tma_load_2d_pair(sB + s * B_BYTES, &tmB, kb * BK, brow, mapa_shared(full_bar(s), 0));
+        else
+          tma_load_2d(sB + s * B_BYTES, &tmB, kb * BK, brow, full_bar(s));
+      };
       bool stop = false;
       for (int n = 0; n < ra.steps && !stop; ++n) {
-        brow = ((ra.buf0 + n) & 1) * ra.Cp + n0;
+        brow = ((ra.buf0 + n) & 1) * ra.Cp + n0 + int(rank) * Cfg::BH;
         a_lo = a_hi = it;
         // A tiles of the first `pre` K-blocks do not depend on the previous step
         for (int kb = 0; kb < pre; ++kb) {
@@ -121,8 +164,7 @@ __global__ void __launch_bounds__(RES_THREADS, 1)
             stop = true;
             break;
           }
-          mbar_arrive_expect_tx(full_bar(s), STAGE_BYTES);
-          tma_load_2d(sA + s * A_BYTES, &tmA, kb * BK, m0, full_bar(s));
+          issue_a(s, kb);
           a_hi = it + kb + 1;
         }
         if (stop) break;
@@ -135,8 +177,7 @@ __global__ void __launch_bounds__(RES_THREADS, 1)
               stop = true;
               break;
             }
-            mbar_arrive_expect_tx(full_bar(s), STAGE_BYTES);
-            tma_load_2d(sA + s * A_BYTES, &tmA, kb * BK, m0, full_bar(s));
+            issue_a(s, kb);
             a_hi = it + 1;
           }
           const int mb = (kb * BK) / BM;  // row block that produced these spins
@@ -148,7 +189,7 @@ __global__ void __launch_bounds__(RES_THREADS, 1)
             fence_proxy_async_global();
             ready_m = mb;
           }
-          tma_load_2d(sB + s * B_BYTES, &tmB, kb * BK, brow, full_bar(s));
+          issue_b(s, kb);
           a_lo = it + 1;
         }
       }
@@ -156,20 +197,27 @@ __global__ void __launch_bounds__(RES_THREADS, 1)
         atomicOr(&s_flag[0], 1);
         // complete every armed slot (the B data is irrelevant now), then wait for
         // all copies this CTA may still have in flight
-        for (int k = a_lo; k < a_hi; ++k)
-          tma_load_2d(sB + (k % STAGES) * B_BYTES, &tmB, 0, brow, full_bar(k % STAGES));
-        for (int k = a_hi - 1; k >= 0 && k >= a_hi - STAGES; --k)
-          (void)mbar_wait(full_bar(k % STAGES), (k / STAGES) & 1, lim);
+        for (int k = a_lo; k < a_hi; ++k) issue_b(k % STAGES, 0);
+        // a pair's odd CTA waits for the MMAs that consume its stages to release
+        // them (bounded: the even CTA may have stopped)
+        for (int k = a_hi - 1; k >= 0 && k >= a_hi - STAGES; --k) {
+          if (!PAIR || leader)
+            (void)mbar_wait(full_bar(k % STAGES), (k / STAGES) & 1, lim);
+          else
+            (void)mbar_wait(empty_bar(k % STAGES), (k / STAGES) & 1, lim);
+        }
       }
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
-    if (lane == 0) {
-      constexpr uint32_t idesc = idesc_bf16<BN>();
+    if (lane == 0 && leader) {
+      constexpr uint32_t idesc = PAIR ? idesc_bf16_m256<BN>() : idesc_bf16<BN>();
       int it = 0;
       int committed = -1;  // last step whose MMAs were committed to acc_full
       for (int n = 0; n < ra.steps; ++n) {
-        if (n > 0 && (!mbar_wait(acc_free, (n - 1) & 1, lim) || *(volatile int*)&s_flag[0])) {
+        const bool freed = n == 0 || (PAIR ? mbar_wait_cluster(acc_free, (n - 1) & 1, lim)
+                                           : mbar_wait(acc_free, (n - 1) & 1, lim));
+        if (!freed || *(volatile int*)&s_flag[0]) {
           atomicOr(&s_flag[0], 1);
           break;
         }
@@ -186,13 +234,24 @@ __global__ void __launch_bounds__(RES_THREADS, 1)
           tc_fence_after();
           if (n == 0 && kb == 0) stamp(a, 2);
 #pragma unroll
-          for (int k = 0; k < BK / 16; ++k)
-            mma_bf16(tmem, sdesc_sw128(sA + s * A_BYTES + k * 32), sdesc_sw128(sB + s * B_BYTES + k * 32), idesc,
-                     (kb | k) != 0);
-          mma_commit(empty_bar(s));
+          for (int k = 0; k < BK / 16; ++k) {
+            const uint64_t da = sdesc_sw128(sA + s * A_BYTES + k * 32);
+            const uint64_t db = sdesc_sw128(sB + s * B_BYTES + k * 32);
+            if (PAIR)
+              mma_bf16_pair(tmem, da, db, idesc, (kb | k) != 0);
+            else
+              mma_bf16(tmem, da, db, idesc, (kb | k) != 0);
+          }
+          if (PAIR)
+            mma_commit_pair(empty_bar(s));  // both CTAs' stages
+          else
+            mma_commit(empty_bar(s));
         }
         if (n == 0) stamp(a, 3);
-        mma_commit(acc_full);  // also after an abort: tracks every MMA issued
+        if (PAIR)  // also after an abort: tracks every MMA issued
+          mma_commit_pair(acc_full);
+        else
+          mma_commit(acc_full);
         committed = n;
         if (stop) break;
       }
@@ -375,7 +434,10 @@ __global__ void __launch_bounds__(RES_THREADS, 1)
       fence_proxy_async_global();
       epi_sync();
       if (e == 0) {
-        mbar_arrive(acc_free);
+        if (PAIR && !leader)
+          mbar_arrive_cluster(mapa_shared(acc_free, 0));
+        else
+          mbar_arrive(acc_free);
         if (n == 0) stamp(a, 5);
       }
       if (e < RPT) {
@@ -426,19 +488,24 @@ __global__ void __launch_bounds__(RES_THREADS, 1)
 
   tc_fence_before();
   __syncthreads();
+  if (PAIR) cluster_sync();  // no CTA leaves while its peer may still signal or read it
   if (threadIdx.x == 0 && s_flag[0]) atomicOr(a.err, E_TIMEOUT);
   if (threadIdx.x == 0) stamp(a, 7);
   if (warp == 1) {
     tc_fence_after();
-    tmem_dealloc(tmem, TMEM_COLS);
+    if (PAIR)
+      tmem_dealloc_pair(tmem, TMEM_COLS);
+    else
+      tmem_dealloc(tmem, TMEM_COLS);
   }
 }
 
-template <bool CPLX>
+template <bool CPLX, bool PAIR>
 cudaError_t launch_res_impl(const CUtensorMap& A, const CUtensorMap& B, const ResArgs& ra, const StepArgs& a,
                             cudaStream_t s) {
+  constexpr uint32_t SMEM = ResCfg<PAIR>::SMEM;
   static bool attr_set = false;
-  auto kern = step_res_kernel<CPLX>;
+  auto kern = step_res_kernel<CPLX, PAIR>;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
     if (e != cudaSuccess) return e;
@@ -450,10 +517,26 @@ cudaError_t launch_res_impl(const CUtensorMap& A, const CUtensorMap& B, const Re
   cfg.dynamicSmemBytes = SMEM;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeCooperative;
-  attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  if (!PAIR) {
+    attr[0].id = cudaLaunchAttributeCooperative;  // every CTA resident: the tile flags need it
+    attr[0].val.cooperative = 1;
+    return cudaLaunchKernelEx(&cfg, kern, A, B, ra, a);
+  }
+  // clusters of the two row blocks of a pair; every cluster resident at once
+  // (the tile flags need it): at most as many clusters as the device holds
+  if (cfg.gridDim.y % 2) return cudaErrorInvalidValue;
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 1;
+  attr[0].val.clusterDim.y = 2;
+  attr[0].val.clusterDim.z = 1;
+  static int max_clusters = 0;
+  if (!max_clusters) {
+    cudaError_t e = cudaOccupancyMaxActiveClusters(&max_clusters, kern, &cfg);
+    if (e != cudaSuccess) return e;
+  }
+  if ((long long)cfg.gridDim.x * cfg.gridDim.y / 2 > max_clusters) return cudaErrorInvalidValue;
   return cudaLaunchKernelEx(&cfg, kern, A, B, ra, a);
 }
 
@@ -463,17 +546,45 @@ bool res_fits(int N, int C, int device) {
   int sms = 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return false;
   int per_sm = 0;
-  auto kern = step_res_kernel<true>;
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM) != cudaSuccess) return false;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, RES_THREADS, SMEM) != cudaSuccess) return false;
+  auto kern = step_res_kernel<true, false>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, ResCfg<false>::SMEM) != cudaSuccess)
+    return false;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, RES_THREADS, ResCfg<false>::SMEM) != cudaSuccess)
+    return false;
   const long long grid = (long long)((C + BN - 1) / BN) * ((N + BM - 1) / BM);
   return per_sm >= 1 && grid <= (long long)per_sm * sms;
 }
 
-cudaError_t launch_step_res(const TcPlan* plan, const ResArgs& ra, const StepArgs& a, cudaStream_t s) {
+bool res_pair_fits(int N, int C) {
+  const int mt = (N + BM - 1) / BM, nt = (C + BN - 1) / BN;
+  if (mt % 2) return false;
+  auto kern = step_res_kernel<true, true>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, ResCfg<true>::SMEM) != cudaSuccess)
+    return false;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nt, mt);
+  cfg.blockDim = dim3(RES_THREADS);
+  cfg.dynamicSmemBytes = ResCfg<true>::SMEM;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 1;
+  attr[0].val.clusterDim.y = 2;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int max_clusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&max_clusters, kern, &cfg) != cudaSuccess) return false;
+  return (long long)nt * mt / 2 <= max_clusters;
+}
+
+cudaError_t launch_step_res(const TcPlan* plan, const ResArgs& ra, const StepArgs& a, cudaStream_t s, bool pair) {
   const CUtensorMap* A = tc_plan_A(plan);
+  if (pair) {
+    const CUtensorMap* B = tc_plan_B64(plan);
+    return a.cplx ? launch_res_impl<true, true>(*A, *B, ra, a, s) : launch_res_impl<false, true>(*A, *B, ra, a, s);
+  }
   const CUtensorMap* B = tc_plan_B(plan);
-  return a.cplx ? launch_res_impl<true>(*A, *B, ra, a, s) : launch_res_impl<false>(*A, *B, ra, a, s);
+  return a.cplx ? launch_res_impl<true, false>(*A, *B, ra, a, s) : launch_res_impl<false, false>(*A, *B, ra, a, s);
 }
 
 }  // namespace gda

@@ -96,6 +96,7 @@ void tc_plan_destroy(TcPlan* plan) { delete plan; }
 
 const CUtensorMap* tc_plan_A(const TcPlan* plan) { return &plan->A; }
 const CUtensorMap* tc_plan_B(const TcPlan* plan) { return &plan->B128; }
+const CUtensorMap* tc_plan_B64(const TcPlan* plan) { return &plan->B64; }
 
 cudaError_t launch_step_tc(const TcPlan* plan, const StepArgs& a, int op_buf, cudaStream_t s, bool pair) {
   return launch_plan<false>(plan, a, op_buf, pair, s);

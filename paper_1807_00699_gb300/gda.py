@@ -18,7 +18,7 @@ ISING, XY = 0, 1
 EULER, RK4 = 0, 1
 FP32, BF16, FP8, SPARSE = 0, 1, 2, 3
 GD, GDMOD = 0, 1  # coupling feedback (gda_coupling_mode)
-AUTO, PER_STEP, RESIDENT, PAIR, STREAM, STREAM_PAIR = 0, 1, 2, 3, 4, 5
+AUTO, PER_STEP, RESIDENT, PAIR, STREAM, STREAM_PAIR, RESIDENT_PAIR = 0, 1, 2, 3, 4, 5, 6
 
 STATUS = {0: "GDA_OK", 1: "GDA_ERR_INVALID", 2: "GDA_ERR_CUDA", 3: "GDA_ERR_OOM", 4: "GDA_ERR_DIVERGED",
           5: "GDA_ERR_TIMEOUT", 6: "GDA_ERR_UNSUPPORTED", 7: "GDA_ERR_STATE"}

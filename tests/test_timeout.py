@@ -68,3 +68,26 @@ def test_wait_limit_is_validated(gda):
             s.run(gda.default_params(**bad), 4, 1)
         assert e.value.status == 1
     s.close()
+
+
+def test_withheld_flag_times_out_in_the_two_sm_form(gda):
+    """The same failure in the resident kernel's two-SM form: the pair's waits
+    on each other (stages counted on the even CTA's barriers, accumulators
+    freed by both epilogues) end on the limit too, and the context recovers."""
+    n, R = 500, 70  # 4 row blocks (2 pairs) x 2 column blocks
+    J, g = synth.xy_gaussian(n, 14)
+    s = gda.Solver(J, g, gda.XY)
+    bad = gda.default_params(dt=0.05, eps=0.1, prec=gda.BF16, schedule=gda.RESIDENT_PAIR, seed=5,
+                             withhold_flag=2, wait_s=0.02)
+    s.run(bad, R, 10)
+    with pytest.raises(gda.GdaError) as e:
+        s.sync()
+    assert e.value.status == 5  # GDA_ERR_TIMEOUT
+    s.sync()
+    kw = dict(dt=0.05, eps=0.1, prec=gda.BF16, seed=5, init_amp=0.2)
+    s.run(gda.default_params(schedule=gda.RESIDENT_PAIR, **kw), R, 1)
+    psi = s.get_state()[0]
+    op = oracle.Params(dt=0.05, eps=0.1, seed=5, init_amp=0.2, operand="bf16")
+    ref = oracle.run(J, g, "xy", op, R, 1)[0]
+    assert np.abs(psi - ref).max() < 1e-5 * max(1.0, np.abs(ref).max())
+    s.close()
