@@ -129,3 +129,20 @@ def test_sparse_rejects_dense_rows(gda):
     assert np.abs(s2.coupling(X, gda.SPARSE) - X @ J2.T).max() < 1e-6
     s.close()
     s2.close()
+
+
+@pytest.mark.parametrize("model,R", [("ising", 5), ("xy", 2)])
+def test_sparse_large_staged_form_matches_oracle(gda, model, R):
+    """N = 14 336: the staged Euler kernel's 1024-thread form (one CTA per SM;
+    a ragged pair for odd R), with noise and the ramp, against the oracle."""
+    n = 14336
+    J = regular3(n, 21)
+    g = 0.05 * synth.normal(22, n) if model == "ising" else 0.05 * synth.normal(23, n)
+    kw = dict(dt=0.02, eps=0.2, eps_hat=0.3, beta0=0.4, noise_D=0.02, seed=6, init_amp=0.3)
+    s = gda.Solver(J, g, gda.XY if model == "xy" else gda.ISING)
+    s.run(gda.default_params(prec=gda.SPARSE, init_mode=1, **kw), R, 3)
+    psi, gam = s.get_state()[:2]
+    ref, rg, _ = oracle.run(J, g, model, oracle.Params(init_mode=1, **kw), R, 3)
+    assert amp_err(psi, ref) < 1e-4
+    assert np.abs(gam - rg).max() < 1e-4 * max(1.0, np.abs(rg).max())
+    s.close()
