@@ -219,8 +219,12 @@ namespace {
 // per-step kernel's order and layout.
 // PAIR_THREADS threads per CTA: 512 where two CTAs share an SM, 1024 where the
 // staged columns take most of an SM's shared memory (more loads in flight).
+// Pairs from split_from on are each swept by split_k CTAs, one contiguous
+// range of tiles each (every one staging the pair): the pairs that would fill
+// only part of the last wave of CTAs are spread over all of it.
 template <bool CPLX, int DW, int PAIR_THREADS>
-__global__ void __launch_bounds__(PAIR_THREADS) k_sparse_euler_pair(StepArgs a, Ell ell) {
+__global__ void __launch_bounds__(PAIR_THREADS) k_sparse_euler_pair(StepArgs a, Ell ell, int split_from,
+                                                                   int split_k) {
   extern __shared__ __align__(16) float xs[];  // [2][Np]: the pair's columns of psi^n
   __shared__ float s_beta[2], s_dsc[2];
   __shared__ int s_bad;
@@ -228,8 +232,16 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_sparse_euler_pair(StepArgs a, 
   constexpr int U = CPLX ? 1 : 2;  // restarts of the pair
   const int tid = threadIdx.x;
   const int Np = a.Np;
-  const int c0 = 2 * blockIdx.x;           // first column of the pair (< Cp)
-  const int r0 = CPLX ? blockIdx.x : c0;   // first restart
+  int pair = blockIdx.x, t_begin = 0, t_end = a.mt_count;
+  if (int(blockIdx.x) >= split_from) {
+    const int idx = int(blockIdx.x) - split_from, ch = idx % split_k;
+    pair = split_from + idx / split_k;
+    t_begin = int((long long)a.mt_count * ch / split_k);
+    t_end = int((long long)a.mt_count * (ch + 1) / split_k);
+  }
+  const bool owner = int(blockIdx.x) < split_from || (int(blockIdx.x) - split_from) % split_k == 0;
+  const int c0 = 2 * pair;                 // first column of the pair (< Cp)
+  const int r0 = CPLX ? pair : c0;         // first restart
   // stage psi^n of both columns: bulk copies of <= 32 KB (Np is a multiple
   // of 128, so every piece is a multiple of 16 bytes and 16-byte aligned)
   const uint32_t bar = ptx::smem_u32(&s_bar);
@@ -268,14 +280,14 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_sparse_euler_pair(StepArgs a, 
   // the two halves of a warp may run different numbers of tiles: shuffles
   // stay within the half
   const unsigned half = (tid & 16) ? 0xffff0000u : 0x0000ffffu;
-  for (int t = grp; t < a.mt_count; t += PAIR_THREADS / 16) {  // 64-row tiles
+  for (int t = t_begin + grp; t < t_end; t += PAIR_THREADS / 16) {  // 64-row tiles
    // the tile's four rows of a thread: every load first (the gathers, the
    // gains, the fields), then the updates and stores, so that no store sits
    // between two loads and a thread keeps all of them in flight
    float y[4][2], gv[4][U], hv[4];
    {  // the next tile's gain lines (two 128-byte lines per restart) into L2
      const int tn = t + PAIR_THREADS / 16;
-     if (tn < a.mt_count && tx < 2 * U && r0 + (tx >> 1) < a.R)
+     if (tn < t_end && tx < 2 * U && r0 + (tx >> 1) < a.R)
        prefetch_l2(a.gam + size_t(r0 + (tx >> 1)) * Np + tn * 64 + 32 * (tx & 1));
    }
 #pragma unroll
@@ -348,7 +360,7 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_sparse_euler_pair(StepArgs a, 
   }
   if (bad) atomicOr(&s_bad, 1);
   __syncthreads();
-  if (tid < U) {
+  if (tid < U && owner) {  // one CTA of a split pair advances its coupling scales
     const int r = r0 + tid;
     if (r < a.R) a.beta_out[r] = next_beta(a, a.beta_in[r]);
   }
@@ -357,14 +369,34 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_sparse_euler_pair(StepArgs a, 
 
 template <bool CPLX, int DW, int NT>
 cudaError_t launch_pair_nt(const StepArgs& a, const Ell& ell, size_t smem, cudaStream_t s) {
+  auto kern = k_sparse_euler_pair<CPLX, DW, NT>;
+  static int slots = 0;  // CTAs of this form resident at once (at the largest staging)
+  static size_t slots_smem = 0;
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_sparse_euler_pair<CPLX, DW, NT>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kPairSmemMax);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kPairSmemMax);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  k_sparse_euler_pair<CPLX, DW, NT><<<(a.C + 1) / 2, NT, smem, s>>>(a, ell);
+  if (slots_smem != smem) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem);
+    if (e != cudaSuccess) return e;
+    slots = sms * per_sm;
+    slots_smem = smem;
+  }
+  // pairs beyond the last full wave are split over the whole of it (k >= 2)
+  const int npairs = (a.C + 1) / 2;
+  const int rem = slots > 0 ? npairs % slots : 0;
+  int k = rem > 0 ? slots / rem : 1;
+  k = k > 8 ? 8 : k;
+  k = k > a.mt_count ? a.mt_count : k;
+  const int split_from = k >= 2 ? npairs - rem : npairs;
+  const int split_k = k >= 2 ? k : 1;
+  const int grid = split_from + (npairs - split_from) * split_k;
+  kern<<<grid, NT, smem, s>>>(a, ell, split_from, split_k);
   return cudaGetLastError();
 }
 
