@@ -253,7 +253,8 @@ def score_arms(arms: dict, base: str) -> dict:
                # first trace point whose tracking energy alone was at or below the target
                "steps_tracking_only": (None if not np.any(a["Et"] <= target)
                                        else int(a["steps"][np.nonzero(a["Et"] <= target)[0][0]])),
-               "E_best_fp64_final": float(a["E_all"].min()), "E_best_fp64_traced": float(a["E64"].min()),
+               "E_best_fp64_final": float(a["E_all"].min()),
+               "E_best_fp64_traced": float(a["E64"].min()) if len(a["E64"]) else None,
                "gap_rel": (float(a["E_all"].min()) - Estar) / abs(Estar),
                "success_prob": float(np.mean(a["E_all"] <= target))}
         if a["extra"] is not None:
