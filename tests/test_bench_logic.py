@@ -51,3 +51,18 @@ def test_energy_trace_without_entries():
     out = bench.score_arms(arms, "y")
     assert out["E_star_fp64"] == -4.0
     assert out["x"]["ttt_s"] is None and out["y"]["steps_to_target"] == 10
+
+
+def test_clock_summary_reads_the_throttle_reasons():
+    c = bench.ClockSampler(0)
+    assert c.summary()["reasons"] == ["unavailable"]
+    na, act = "Not Active", "Active"
+    c.samples = [["1695", "2070", "1390.2", na, na, na, act],
+                 ["1650", "2070", "1398.0", na, na, na, act],
+                 ["2070", "2070", "900.5", na, na, na, na],
+                 ["[N/A]", "2070", "[N/A]", na, na, na, na]]
+    s = c.summary()
+    assert s["sm_mhz"] == 1695.0 and s["sm_max_mhz"] == 2070.0 and s["samples"] == 4
+    assert s["reasons"] == ["sw_power_cap"]
+    c.samples.append(["1200", "2070", "1000", na, act, na, na])
+    assert bench.ClockSampler.summary(c)["reasons"] == ["hw_thermal_slowdown", "sw_power_cap"]
